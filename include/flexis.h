@@ -1,0 +1,247 @@
+/*
+ * flexis.h -- C ABI of the GB300 support-evaluation library for FLEXIS frequent subgraph mining
+ * (arXiv 2404.01585).
+ *
+ * The library keeps one vertex-labelled data graph resident on one GPU and evaluates the
+ * support of candidate patterns in it: the greedy maximal-independent-set count (mIS) of the
+ * pattern's maps (Sec. 2.4.3; matcher of Sec. 3.2.2), the minimum-image count (MNI, Sec. 2.4.4)
+ * and the frequent decision against the lambda-slider threshold tau (Eq. tau, Sec. 3.1.1).  On
+ * top it runs the level-wise mining loop (Algorithm 1) with candidate generation by merging
+ * (Algorithms 2-4, Sec. 3.2.1) and a request-serving loop.
+ *
+ * Conventions (every entry point):
+ *   - Return value: FLEXIS_OK (0) or a negative FLEXIS_E_* code; outputs are written only on OK.
+ *     flexis_status_string() names a code.  Errors are also reported per pattern in the
+ *     `status` field of results.
+ *   - Ownership: the caller owns every input array and may free it once the call returns (the
+ *     library copies what it keeps).  Handles (flexis_graph, flexis_pattern_set, flexis_server)
+ *     are owned by the library and released with the matching flexis_free_* / _stop call.
+ *   - Threading: a flexis_graph is thread-compatible, not thread-safe: calls on one handle must
+ *     not overlap.  Different handles are independent.  A server owns its own host thread.
+ *   - Pointers are host pointers unless the parameter name starts with `d_` (device pointer on
+ *     the graph's GPU).
+ *   - Exactness: every count is an integer computed exactly; results do not depend on batch
+ *     composition, launch shape or the order in which requests arrive.
+ *
+ * Semantics fixed by this library where the paper leaves a choice open:
+ *   - Labels: the labels present in the data graph are ranked by ascending frequency (ties by
+ *     id); patterns are canonicalised over ranks.  A pattern label absent from the graph gives
+ *     mis = mni = 0 and frequent = 0.
+ *   - Which maximal independent set (the paper allows any, Sec. 2.4.3): maps are taken in the
+ *     order (H(seed, root), root, lexicographic tuple in matching order), root = image of
+ *     canonical vertex 0, H = one SplitMix64 step from state seed XOR root.  Per root the first
+ *     map avoiding used vertices is selected and the root's search stops (Sec. 3.2.2, change 1);
+ *     used vertices are shared across roots (Sec. 3.2.2, change 2).
+ *   - tau = floor(sigma * ((n-1) * p + q) / (n * q)) exactly, lambda = p / q, q = 10^6 and
+ *     p = llround(lambda * 10^6) for the double-valued entry points.
+ *   - Frequent <=> mIS >= max(tau, 1).
+ */
+#ifndef FLEXIS_H
+#define FLEXIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define FLEXIS_OK 0
+#define FLEXIS_E_INVALID (-1)     /* bad argument: out-of-range id, disconnected pattern, n<2 or
+                                     n>8, lambda outside [0,1] or NaN, sigma < 1, null pointer */
+#define FLEXIS_E_NOMEM (-2)       /* a host or device allocation failed */
+#define FLEXIS_E_CUDA (-3)        /* a CUDA runtime call failed (no device, launch error) */
+#define FLEXIS_E_TIMEOUT (-4)     /* a bounded device or host wait gave up */
+#define FLEXIS_E_CANCELLED (-5)   /* a served request was cancelled / server stopped */
+#define FLEXIS_E_UNSUPPORTED (-6) /* graph beyond the layout limits (see flexis_load_graph) */
+#define FLEXIS_E_BUSY (-7)        /* serving queue full; retry later */
+
+/* ------------------------------------------------------------------ modes */
+#define FLEXIS_MODE_FULL 0  /* exact mIS and exact MNI */
+#define FLEXIS_MODE_EARLY 1 /* stop at c = max(tau,1) (Sec. 3.1.1): mis = min(mIS, c),
+                               mni = min(MNI, c); the frequent decision is unchanged */
+
+/* result flags */
+#define FLEXIS_FLAG_ABSENT_LABEL 1u /* a pattern label does not occur in the data graph */
+#define FLEXIS_FLAG_MNI_FROM_MIS 2u /* mni follows from mis (mis reached c, or M is empty) */
+
+#define FLEXIS_MAX_PATTERN 8 /* largest pattern, in vertices */
+
+typedef struct flexis_graph flexis_graph;
+typedef struct flexis_pattern_set flexis_pattern_set;
+typedef struct flexis_server flexis_server;
+
+typedef struct {
+    uint64_t seed;        /* greedy-order seed (default 0x5EED) */
+    int32_t device;       /* CUDA device ordinal (default 0) */
+    int32_t window_min;   /* speculation window per pattern: 0 = autotuned */
+    int32_t window_max;   /* 0 = autotuned */
+    int32_t search_blocks;/* blocks of the search kernel: 0 = autotuned (multiple of the SM count) */
+    int32_t record_selected; /* >0: keep up to this many selected maps per pattern (tests) */
+    int32_t reserved[9];
+} flexis_options;
+
+/* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
+ * edges edges[2*m] as 0-based vertex pairs.  Repeated edges are allowed and merged; self-loops
+ * and disconnected patterns are FLEXIS_E_INVALID.  2 <= n <= 8.                                */
+typedef struct {
+    int32_t n;
+    int32_t m;
+    const int32_t *labels;
+    const int32_t *edges;
+} flexis_pattern;
+
+/* Support of one pattern (all integer). */
+typedef struct {
+    int32_t status;   /* FLEXIS_OK or an error code for this pattern */
+    int32_t n;        /* pattern vertices */
+    int64_t sigma;
+    int64_t tau;      /* Eq. tau */
+    int64_t cap;      /* EARLY: max(tau,1); FULL: -1 */
+    int64_t mis;      /* greedy maximal independent set size (capped in EARLY mode) */
+    int64_t mni;      /* minimum image count (capped in EARLY mode) */
+    int32_t frequent; /* mis >= max(tau, 1) */
+    uint32_t flags;   /* FLEXIS_FLAG_* */
+    int64_t roots_searched; /* diagnostic: root searches run (not part of the result) */
+} flexis_support_result;
+
+/* Precompiled pattern (host-side pattern compilation: canonical form, automorphism orbits,
+ * matching orders, tau).  Plain bytes: may be copied to device memory and passed to
+ * flexis_support_plans_device.                                                                 */
+typedef struct {
+    uint8_t bytes[512];
+} flexis_plan;
+
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_arcs;           /* directed arcs kept (2 x undirected edges) */
+    int64_t n_self_loops;     /* dropped */
+    int64_t n_duplicates;     /* dropped (undirected repeats) */
+    int32_t n_labels;         /* labels present */
+    int32_t max_degree;
+    int64_t device_bytes;     /* device memory held by the graph */
+    int32_t sm_count;
+    int32_t l2_bytes;
+} flexis_graph_info;
+
+/* Counters of the last support / batch / mining call on a graph (diagnostics, timing). */
+typedef struct {
+    int64_t rounds;           /* speculation rounds */
+    int64_t search_items;     /* root searches run by the search kernel */
+    int64_t mni_items;        /* existence searches run by the MNI kernel */
+    int64_t kernel_launches;  /* kernels launched by the call */
+    int64_t alg_bytes;        /* algorithmic bytes read by the search kernels (adjacency entries,
+                                 label-run entries, vertex records, used-bitmap words) */
+    int64_t alg_bytes_greedy; /* part of alg_bytes read by the greedy search kernel */
+    float search_ms;          /* summed CUDA-event time of the greedy search kernel launches */
+    float mni_ms;             /* CUDA-event time of the MNI kernel */
+    float total_ms;           /* CUDA-event time of the whole device section */
+    int32_t search_launches;  /* launches of the greedy search kernel */
+    int32_t pad;
+} flexis_stats;
+
+const char *flexis_status_string(int status);
+
+/* Fill *opt with the defaults. */
+void flexis_default_options(flexis_options *opt);
+
+/* Load a data graph (Sec. 2.2: single large vertex-labelled graph; undirected, as the paper's
+ * loader, Sec. 4.1).  labels[n_vertices] >= 0; src/dst[n_edges] vertex ids in [0, n_vertices).
+ * Self-loops and repeated edges are dropped (counted in flexis_graph_info).  The graph is kept
+ * on the device as a CSR with adjacency sorted by (label rank, id), a per-vertex label-run table
+ * and a label-partitioned vertex index in greedy-root order.
+ * Layout limits (FLEXIS_E_UNSUPPORTED beyond them): fewer than 255 distinct labels present,
+ * n_vertices < 2^31, directed arcs < 2^32, vertex degree < 2^24.  opt may be NULL.             */
+int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
+                      const int32_t *src, const int32_t *dst, const flexis_options *opt,
+                      flexis_graph **out);
+void flexis_free_graph(flexis_graph *g);
+int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out);
+
+/* Support of one pattern (Sec. 2.4, Eq. tau): one plain evaluation, launched and synchronised
+ * on its own.  lambda in [0,1]; mode FLEXIS_MODE_EARLY or FLEXIS_MODE_FULL.                    */
+int flexis_support(flexis_graph *g, const flexis_pattern *pattern, int64_t sigma, double lambda,
+                   int32_t mode, flexis_support_result *out);
+
+/* Same with lambda = lambda_num / lambda_den exactly. */
+int flexis_support_q(flexis_graph *g, const flexis_pattern *pattern, int64_t sigma,
+                     int64_t lambda_num, int64_t lambda_den, int32_t mode,
+                     flexis_support_result *out);
+
+/* Supports of `count` patterns evaluated together (all candidates of a mining level,
+ * Algorithm 1 / Algorithm 5 loop): one batched device pass.  sigma[count], lambda[count].
+ * Per-pattern errors go to out[i].status; the call fails only on device errors.                */
+int flexis_support_batch(flexis_graph *g, const flexis_pattern *patterns, const int64_t *sigma,
+                         const double *lambda, int32_t count, int32_t mode,
+                         flexis_support_result *out);
+
+/* Host-side pattern compilation into plans (see flexis_plan).  Per-pattern errors are stored
+ * in the plan and reported by the evaluation; returns FLEXIS_E_INVALID only for bad arrays.    */
+int flexis_compile(flexis_graph *g, const flexis_pattern *patterns, const int64_t *sigma,
+                   const int64_t *lambda_num, int64_t lambda_den, int32_t count, int32_t mode,
+                   flexis_plan *plans_out);
+
+/* Batched evaluation of plans already resident in device memory; results written to device
+ * memory d_results[count].  Runs on `stream` (a cudaStream_t, NULL = the graph's stream) and
+ * returns after the results are written (the call synchronises the stream).                    */
+int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int32_t count,
+                                flexis_support_result *d_results, void *stream);
+
+/* Counters of the last evaluation call on g. */
+int flexis_last_stats(const flexis_graph *g, flexis_stats *out);
+
+/* Selected maps recorded by the last evaluation when opt.record_selected > 0: for pattern i,
+ * up to `cap` maps of 8 ids each (canonical-vertex order, in selection order) into maps_out;
+ * *n_out gets their number.                                                                    */
+int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,
+                         int64_t *n_out);
+
+/* Mining (Algorithm 1): level 2 = label pairs present on data edges; each level evaluated as
+ * one batch in EARLY mode; next candidates by merging (Algorithms 2-4, Sec. 3.2.1) with
+ * canonical-code duplicate removal; levels k = 2 .. max_edges+1 vertices, keeping candidates
+ * with at most max_edges edges.  The set is sorted by (n, canonical code).                     */
+int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges,
+                flexis_pattern_set **out);
+int64_t flexis_pattern_set_count(const flexis_pattern_set *s);
+/* i-th frequent pattern in canonical form: *n, labels[8] (label ids), *m, edges[2*28],
+ * rank-space canonical code (code_labels[8] ranks, *code_bits), and its support result.        */
+int flexis_pattern_set_get(const flexis_pattern_set *s, int64_t i, int32_t *n, int32_t *labels,
+                           int32_t *m, int32_t *edges, int32_t *code_labels, uint32_t *code_bits,
+                           flexis_support_result *result);
+/* per level k (0..8): candidates evaluated and frequent patterns found */
+int flexis_pattern_set_levels(const flexis_pattern_set *s, int64_t *candidates, int64_t *frequent);
+void flexis_free_pattern_set(flexis_pattern_set *s);
+
+/* Canonical code of a pattern with its labels used as given (the form that replaces Bliss's,
+ * Sec. 2.1.5): labels in canonical order, adjacency bits, and perm[p] = input vertex at
+ * canonical position p.                                                                        */
+int flexis_canonical_code(const flexis_pattern *pattern, int32_t *labels_out, uint32_t *bits_out,
+                          int32_t *perm_out);
+
+/* Candidate generation by core-group merging (Algorithms 2-4) on patterns given with labels
+ * used as given.  Writes sorted canonical codes (n, labels[8], bits) of the candidates; returns
+ * their number, or -(number) if cap is too small.  max_edges <= 0: no edge limit.            */
+int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count,
+                                   int32_t max_edges, int32_t *n_out, int32_t *labels_out,
+                                   uint32_t *bits_out, int64_t cap);
+
+/* ------------------------------------------------------------------ serving
+ * A server keeps the graph resident and evaluates support requests as they arrive
+ * (continuous batching): requests are admitted into device slots while earlier ones are still
+ * being evaluated, and share the device rounds with them.  Admission is bounded by `slots`
+ * and by the estimated device memory of a request.                                             */
+int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out);
+/* Queue a request; copies the pattern.  FLEXIS_E_BUSY if the host queue is full. */
+int flexis_serve_submit(flexis_server *s, int64_t request_id, const flexis_pattern *pattern,
+                        int64_t sigma, double lambda, int32_t mode);
+/* Take up to `max` finished results; ids[i] is the request id of results[i]; latency_us[i] the
+ * time from submit to completion (nullable). Non-blocking.                                     */
+int flexis_serve_poll(flexis_server *s, int64_t *ids, flexis_support_result *results,
+                      double *latency_us, int32_t max, int32_t *n_out);
+/* Stop: pending requests finish with FLEXIS_E_CANCELLED.  Frees the server. */
+int flexis_serve_stop(flexis_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLEXIS_H */
