@@ -1,0 +1,373 @@
+"""Python binding of libflexis.so (the C ABI in include/flexis.h).
+
+Argument marshalling only: every step of support evaluation runs in the library's CUDA kernels
+and host runtime.  There is no fallback: if the compiled library is missing, importing the
+binding's entry points raises.
+
+Function names follow the C ABI (flexis_load_graph, flexis_support, flexis_support_batch,
+flexis_mine, flexis_serve_*, ...); `Graph` and `Server` wrap the handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libflexis.so")
+
+FLEXIS_OK = 0
+FLEXIS_E_INVALID = -1
+FLEXIS_E_NOMEM = -2
+FLEXIS_E_CUDA = -3
+FLEXIS_E_TIMEOUT = -4
+FLEXIS_E_CANCELLED = -5
+FLEXIS_E_UNSUPPORTED = -6
+FLEXIS_E_BUSY = -7
+FLEXIS_MODE_FULL = 0
+FLEXIS_MODE_EARLY = 1
+FLEXIS_FLAG_ABSENT_LABEL = 1
+FLEXIS_FLAG_MNI_FROM_MIS = 2
+LAMBDA_DEN = 1_000_000
+DEFAULT_SEED = 0x5EED
+
+
+class FlexisError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class flexis_options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("device", C.c_int32), ("window_min", C.c_int32),
+                ("window_max", C.c_int32), ("search_blocks", C.c_int32),
+                ("record_selected", C.c_int32), ("reserved", C.c_int32 * 9)]
+
+
+class flexis_pattern(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("labels", C.POINTER(C.c_int32)),
+                ("edges", C.POINTER(C.c_int32))]
+
+
+class flexis_support_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("sigma", C.c_int64), ("tau", C.c_int64),
+                ("cap", C.c_int64), ("mis", C.c_int64), ("mni", C.c_int64),
+                ("frequent", C.c_int32), ("flags", C.c_uint32), ("roots_searched", C.c_int64)]
+
+    def as_dict(self):
+        return dict(status=self.status, n=self.n, sigma=self.sigma, tau=self.tau, cap=self.cap,
+                    mis=self.mis, mni=self.mni, frequent=bool(self.frequent), flags=self.flags,
+                    roots_searched=self.roots_searched)
+
+
+class flexis_plan(C.Structure):
+    _fields_ = [("bytes", C.c_uint8 * 512)]
+
+
+class flexis_graph_info(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("n_arcs", C.c_int64), ("n_self_loops", C.c_int64),
+                ("n_duplicates", C.c_int64), ("n_labels", C.c_int32), ("max_degree", C.c_int32),
+                ("device_bytes", C.c_int64), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32)]
+
+
+class flexis_stats(C.Structure):
+    _fields_ = [("rounds", C.c_int64), ("search_items", C.c_int64), ("mni_items", C.c_int64),
+                ("kernel_launches", C.c_int64), ("alg_bytes", C.c_int64),
+                ("alg_bytes_greedy", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
+                ("total_ms", C.c_float), ("search_launches", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+# symbol table: name -> (restype, argtypes); every symbol include/flexis.h declares
+_P = C.c_void_p
+_I32P = C.POINTER(C.c_int32)
+_I64P = C.POINTER(C.c_int64)
+SYMBOLS = {
+    "flexis_status_string": (C.c_char_p, [C.c_int]),
+    "flexis_default_options": (None, [C.POINTER(flexis_options)]),
+    "flexis_load_graph": (C.c_int, [C.c_int64, _I32P, C.c_int64, _I32P, _I32P,
+                                     C.POINTER(flexis_options), C.POINTER(_P)]),
+    "flexis_free_graph": (None, [_P]),
+    "flexis_graph_info_get": (C.c_int, [_P, C.POINTER(flexis_graph_info)]),
+    "flexis_support": (C.c_int, [_P, C.POINTER(flexis_pattern), C.c_int64, C.c_double, C.c_int32,
+                                  C.POINTER(flexis_support_result)]),
+    "flexis_support_q": (C.c_int, [_P, C.POINTER(flexis_pattern), C.c_int64, C.c_int64, C.c_int64,
+                                    C.c_int32, C.POINTER(flexis_support_result)]),
+    "flexis_support_batch": (C.c_int, [_P, C.POINTER(flexis_pattern), _I64P, C.POINTER(C.c_double),
+                                        C.c_int32, C.c_int32, C.POINTER(flexis_support_result)]),
+    "flexis_compile": (C.c_int, [_P, C.POINTER(flexis_pattern), _I64P, _I64P, C.c_int64, C.c_int32,
+                                  C.c_int32, C.POINTER(flexis_plan)]),
+    "flexis_support_plans_device": (C.c_int, [_P, _P, C.c_int32, _P, _P]),
+    "flexis_last_stats": (C.c_int, [_P, C.POINTER(flexis_stats)]),
+    "flexis_selected_maps": (C.c_int, [_P, C.c_int32, _I32P, C.c_int64, _I64P]),
+    "flexis_mine": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int32, C.POINTER(_P)]),
+    "flexis_pattern_set_count": (C.c_int64, [_P]),
+    "flexis_pattern_set_get": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P, _I32P, _I32P,
+                                          C.POINTER(C.c_uint32), C.POINTER(flexis_support_result)]),
+    "flexis_pattern_set_levels": (C.c_int, [_P, _I64P, _I64P]),
+    "flexis_free_pattern_set": (None, [_P]),
+    "flexis_canonical_code": (C.c_int, [C.POINTER(flexis_pattern), _I32P, C.POINTER(C.c_uint32), _I32P]),
+    "flexis_generate_candidates": (C.c_int64, [C.POINTER(flexis_pattern), C.c_int32, C.c_int32, _I32P,
+                                               _I32P, C.POINTER(C.c_uint32), C.c_int64]),
+    "flexis_serve_start": (C.c_int, [_P, C.c_int32, C.POINTER(_P)]),
+    "flexis_serve_submit": (C.c_int, [_P, C.c_int64, C.POINTER(flexis_pattern), C.c_int64,
+                                       C.c_double, C.c_int32]),
+    "flexis_serve_poll": (C.c_int, [_P, _I64P, C.POINTER(flexis_support_result),
+                                     C.POINTER(C.c_double), C.c_int32, _I32P]),
+    "flexis_serve_stop": (C.c_int, [_P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libflexis.so.  Raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libflexis.so is not built ({LIB_PATH}); run "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SYMBOLS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().flexis_status_string(code).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(code, what):
+    if code != FLEXIS_OK:
+        raise FlexisError(code, what)
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+
+
+def make_pattern(labels, edges):
+    """(flexis_pattern, keepalive) from label list and edge list."""
+    lab = _i32(labels)
+    e = _i32(np.asarray(edges, dtype=np.int32).reshape(-1)) if len(edges) else np.zeros(2, np.int32)
+    m = (e.size // 2) if len(edges) else 0
+    p = flexis_pattern(lab.size, m, lab.ctypes.data_as(_I32P), e.ctypes.data_as(_I32P))
+    return p, (lab, e)
+
+
+def default_options(**kw) -> flexis_options:
+    o = flexis_options()
+    lib().flexis_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "timing":
+            o.reserved[0] = 1 if v else 0
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A data graph resident on one GPU (flexis_load_graph)."""
+
+    def __init__(self, labels, src, dst, **options):
+        L = lib()
+        self._labels = _i32(labels)
+        self._src = _i32(src)
+        self._dst = _i32(dst)
+        self.options = default_options(**options)
+        h = _P()
+        ne = self._src.size
+        srcp = self._src if ne else np.zeros(1, np.int32)
+        dstp = self._dst if ne else np.zeros(1, np.int32)
+        rc = L.flexis_load_graph(self._labels.size, self._labels.ctypes.data_as(_I32P), ne,
+                                 srcp.ctypes.data_as(_I32P), dstp.ctypes.data_as(_I32P),
+                                 C.byref(self.options), C.byref(h))
+        _check(rc, "flexis_load_graph")
+        self._h = h
+        del self._src, self._dst
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flexis_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = flexis_graph_info()
+        _check(lib().flexis_graph_info_get(self._h, C.byref(i)), "flexis_graph_info_get")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def support(self, labels, edges, sigma, lam=None, *, lam_num=None, lam_den=LAMBDA_DEN,
+                mode=FLEXIS_MODE_EARLY) -> dict:
+        p, keep = make_pattern(labels, edges)
+        r = flexis_support_result()
+        if lam_num is not None:
+            rc = lib().flexis_support_q(self._h, C.byref(p), sigma, lam_num, lam_den, mode, C.byref(r))
+        else:
+            rc = lib().flexis_support(self._h, C.byref(p), sigma, float(lam), mode, C.byref(r))
+        _check(rc, "flexis_support")
+        return r.as_dict()
+
+    def _patterns(self, patterns):
+        arr = (flexis_pattern * max(1, len(patterns)))()
+        keep = []
+        for i, (l, e) in enumerate(patterns):
+            p, k = make_pattern(l, e)
+            arr[i] = p
+            keep.append(k)
+        return arr, keep
+
+    def support_batch(self, patterns, sigma, lam, mode=FLEXIS_MODE_EARLY) -> list[dict]:
+        cnt = len(patterns)
+        arr, keep = self._patterns(patterns)
+        sig = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.int64), (cnt,)))
+        lm = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (cnt,)))
+        out = (flexis_support_result * max(1, cnt))()
+        rc = lib().flexis_support_batch(self._h, arr, sig.ctypes.data_as(_I64P),
+                                        lm.ctypes.data_as(C.POINTER(C.c_double)), cnt, mode, out)
+        _check(rc, "flexis_support_batch")
+        return [out[i].as_dict() for i in range(cnt)]
+
+    def compile(self, patterns, sigma, lam, mode=FLEXIS_MODE_EARLY) -> np.ndarray:
+        """Plans (uint8 [count, 512]) of the patterns, ready to be copied to device memory."""
+        cnt = len(patterns)
+        arr, keep = self._patterns(patterns)
+        sig = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.int64), (cnt,)))
+        num = np.ascontiguousarray(np.rint(np.broadcast_to(np.asarray(lam, np.float64), (cnt,)) * LAMBDA_DEN).astype(np.int64))
+        plans = np.zeros((max(1, cnt), 512), np.uint8)
+        rc = lib().flexis_compile(self._h, arr, sig.ctypes.data_as(_I64P), num.ctypes.data_as(_I64P),
+                                  LAMBDA_DEN, cnt, mode, plans.ctypes.data_as(C.POINTER(flexis_plan)))
+        _check(rc, "flexis_compile")
+        return plans[:cnt]
+
+    def support_plans_device(self, d_plans_ptr: int, count: int, d_results_ptr: int, stream_ptr: int = 0):
+        rc = lib().flexis_support_plans_device(self._h, C.c_void_p(d_plans_ptr), count,
+                                               C.c_void_p(d_results_ptr), C.c_void_p(stream_ptr))
+        _check(rc, "flexis_support_plans_device")
+
+    def stats(self) -> dict:
+        s = flexis_stats()
+        _check(lib().flexis_last_stats(self._h, C.byref(s)), "flexis_last_stats")
+        return s.as_dict()
+
+    def selected_maps(self, i: int, n: int, cap: int = 1 << 20):
+        buf = np.zeros((cap, 8), np.int32)
+        k = C.c_int64()
+        _check(lib().flexis_selected_maps(self._h, i, buf.ctypes.data_as(_I32P), cap, C.byref(k)),
+               "flexis_selected_maps")
+        return [tuple(int(x) for x in buf[j, :n]) for j in range(k.value)]
+
+    def mine(self, sigma, lam, max_edges):
+        """Algorithm 1.  Returns (patterns, levels): patterns = list of dict(n, labels, edges,
+        code_labels, code_bits, tau, mis, mni) sorted by (n, canonical code); levels maps
+        k -> (candidates, frequent)."""
+        L = lib()
+        h = _P()
+        _check(L.flexis_mine(self._h, sigma, float(lam), max_edges, C.byref(h)), "flexis_mine")
+        try:
+            cnt = L.flexis_pattern_set_count(h)
+            out = []
+            n = C.c_int32()
+            m = C.c_int32()
+            lab = np.zeros(8, np.int32)
+            clab = np.zeros(8, np.int32)
+            edg = np.zeros(56, np.int32)
+            bits = C.c_uint32()
+            r = flexis_support_result()
+            for i in range(cnt):
+                _check(L.flexis_pattern_set_get(h, i, C.byref(n), lab.ctypes.data_as(_I32P), C.byref(m),
+                                                edg.ctypes.data_as(_I32P), clab.ctypes.data_as(_I32P),
+                                                C.byref(bits), C.byref(r)), "flexis_pattern_set_get")
+                d = r.as_dict()
+                d.update(n=n.value, labels=tuple(int(x) for x in lab[: n.value]),
+                         edges=[(int(edg[2 * j]), int(edg[2 * j + 1])) for j in range(m.value)],
+                         code_labels=tuple(int(x) for x in clab[: n.value]), code_bits=int(bits.value))
+                out.append(d)
+            cand = np.zeros(9, np.int64)
+            freq = np.zeros(9, np.int64)
+            L.flexis_pattern_set_levels(h, cand.ctypes.data_as(_I64P), freq.ctypes.data_as(_I64P))
+            levels = {k: (int(cand[k]), int(freq[k])) for k in range(2, 9) if cand[k] > 0}
+            return out, levels
+        finally:
+            L.flexis_free_pattern_set(h)
+
+
+def canonical_code(labels, edges):
+    p, keep = make_pattern(labels, edges)
+    n = p.n
+    lab = np.zeros(max(n, 1), np.int32)
+    perm = np.zeros(max(n, 1), np.int32)
+    bits = C.c_uint32()
+    _check(lib().flexis_canonical_code(C.byref(p), lab.ctypes.data_as(_I32P), C.byref(bits),
+                                       perm.ctypes.data_as(_I32P)), "flexis_canonical_code")
+    return tuple(int(x) for x in lab[:n]), int(bits.value), tuple(int(x) for x in perm[:n])
+
+
+def generate_candidates(patterns, max_edges=0):
+    arr = (flexis_pattern * max(1, len(patterns)))()
+    keep = []
+    for i, (l, e) in enumerate(patterns):
+        p, k = make_pattern(l, e)
+        arr[i] = p
+        keep.append(k)
+    cap = 1 << 18
+    on = np.zeros(cap, np.int32)
+    ol = np.zeros(cap * 8, np.int32)
+    ob = np.zeros(cap, np.uint32)
+    k = lib().flexis_generate_candidates(arr, len(patterns), max_edges, on.ctypes.data_as(_I32P),
+                                         ol.ctypes.data_as(_I32P),
+                                         ob.ctypes.data_as(C.POINTER(C.c_uint32)), cap)
+    if k < 0:
+        raise FlexisError(FLEXIS_E_INVALID if k == -1 else FLEXIS_E_NOMEM, "flexis_generate_candidates")
+    return [(int(on[i]), tuple(int(x) for x in ol[8 * i: 8 * i + on[i]]), int(ob[i])) for i in range(k)]
+
+
+class Server:
+    """Continuous-batching support server on a resident graph (flexis_serve_*)."""
+
+    def __init__(self, graph: Graph, slots: int = 0):
+        h = _P()
+        _check(lib().flexis_serve_start(graph.handle, slots, C.byref(h)), "flexis_serve_start")
+        self._h = h
+        self.graph = graph
+
+    def submit(self, request_id, labels, edges, sigma, lam, mode=FLEXIS_MODE_EARLY):
+        p, keep = make_pattern(labels, edges)
+        return lib().flexis_serve_submit(self._h, request_id, C.byref(p), sigma, float(lam), mode)
+
+    def poll(self, max_results=4096):
+        ids = np.zeros(max_results, np.int64)
+        res = (flexis_support_result * max_results)()
+        lat = np.zeros(max_results, np.float64)
+        n = C.c_int32()
+        rc = lib().flexis_serve_poll(self._h, ids.ctypes.data_as(_I64P), res,
+                                     lat.ctypes.data_as(C.POINTER(C.c_double)), max_results, C.byref(n))
+        _check(rc, "flexis_serve_poll")
+        return [(int(ids[i]), res[i].as_dict(), float(lat[i])) for i in range(n.value)]
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            rc = lib().flexis_serve_stop(self._h)
+            self._h = None
+            _check(rc, "flexis_serve_stop")

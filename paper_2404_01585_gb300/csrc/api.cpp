@@ -1,0 +1,516 @@
+// C ABI of the FLEXIS GB300 library (declared in include/flexis.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "fx_dev.h"
+
+using namespace fx;
+
+struct flexis_graph {
+    HostGraph hg;
+    DeviceGraph *dg = nullptr;
+    flexis_options opt{};
+    flexis_stats last{};
+};
+
+struct flexis_pattern_set {
+    struct Entry {
+        Code code;  // rank-space canonical code
+        flexis_support_result res;
+    };
+    std::vector<Entry> items;
+    std::vector<int32_t> label_of_rank;
+    int64_t cand[FLEXIS_MAX_PATTERN + 1] = {0};
+    int64_t freq[FLEXIS_MAX_PATTERN + 1] = {0};
+};
+
+namespace {
+
+constexpr int64_t LAMBDA_DEN = 1000000;
+
+bool lambda_to_q(double lambda, int64_t *num) {
+    if (!(lambda >= 0.0 && lambda <= 1.0)) return false;  // also rejects NaN
+    *num = llround(lambda * (double)LAMBDA_DEN);
+    return true;
+}
+
+// Autotuned launch shape: many patterns -> small windows (parallelism comes from the batch);
+// few patterns -> large windows (parallelism has to come from speculation).
+EvalConfig config_for(const flexis_graph *g, int32_t P) {
+    EvalConfig c;
+    int wmax = P >= 64 ? 512 : 1024;
+    int wmin = std::max(16, std::min(wmax, 16384 / std::max(1, P)));
+    if (g->opt.window_max > 0) wmax = g->opt.window_max;
+    if (g->opt.window_min > 0) wmin = g->opt.window_min;
+    c.w_min = std::min(wmin, wmax);
+    c.w_max = wmax;
+    c.search_blocks = g->opt.search_blocks;
+    c.record_selected = g->opt.record_selected;
+    c.rounds_per_sync = P >= 64 ? 4 : 2;
+    c.timing = g->opt.reserved[0] != 0;
+    return c;
+}
+
+int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result *out) {
+    EvalConfig cfg = config_for(g, (int32_t)plans.size());
+    return dev_eval_host(g->dg, plans.data(), (int32_t)plans.size(), out, cfg, &g->last);
+}
+
+void pattern_of_code(const flexis_graph *g, const Code &c, std::vector<int32_t> &labels,
+                     std::vector<int32_t> &edges) {
+    Pat p = pat_of_code(c);
+    labels.resize((size_t)p.n);
+    edges.clear();
+    for (int i = 0; i < p.n; i++) {
+        labels[(size_t)i] = g->hg.label_of_rank[(size_t)p.lab[i]];
+        for (int j = i + 1; j < p.n; j++)
+            if (p.adj[i] >> j & 1) {
+                edges.push_back(i);
+                edges.push_back(j);
+            }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *flexis_status_string(int status) {
+    switch (status) {
+        case FLEXIS_OK: return "ok";
+        case FLEXIS_E_INVALID: return "invalid argument";
+        case FLEXIS_E_NOMEM: return "out of memory";
+        case FLEXIS_E_CUDA: return "CUDA error";
+        case FLEXIS_E_TIMEOUT: return "timeout";
+        case FLEXIS_E_CANCELLED: return "cancelled";
+        case FLEXIS_E_UNSUPPORTED: return "unsupported graph layout";
+        case FLEXIS_E_BUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+void flexis_default_options(flexis_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof *opt);
+    opt->seed = DEFAULT_SEED;
+    opt->device = 0;
+}
+
+int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
+                      const int32_t *src, const int32_t *dst, const flexis_options *opt,
+                      flexis_graph **out) {
+    if (!out) return FLEXIS_E_INVALID;
+    std::unique_ptr<flexis_graph> g(new (std::nothrow) flexis_graph());
+    if (!g) return FLEXIS_E_NOMEM;
+    if (opt) g->opt = *opt; else flexis_default_options(&g->opt);
+    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->hg);
+    if (rc) return rc;
+    rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
+    if (rc) return rc;
+    *out = g.release();
+    return FLEXIS_OK;
+}
+
+void flexis_free_graph(flexis_graph *g) {
+    if (!g) return;
+    dev_graph_destroy(g->dg);
+    delete g;
+}
+
+int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out) {
+    if (!g || !out) return FLEXIS_E_INVALID;
+    memset(out, 0, sizeof *out);
+    out->n_vertices = g->hg.nv;
+    out->n_arcs = g->hg.n_arcs;
+    out->n_self_loops = g->hg.self_loops;
+    out->n_duplicates = g->hg.duplicates;
+    out->n_labels = g->hg.nl;
+    out->max_degree = g->hg.max_degree;
+    out->device_bytes = dev_graph_bytes(g->dg);
+    int sm = 0, l2 = 0;
+    dev_graph_props(g->dg, &sm, &l2);
+    out->sm_count = sm;
+    out->l2_bytes = l2;
+    return FLEXIS_OK;
+}
+
+int flexis_support_q(flexis_graph *g, const flexis_pattern *pattern, int64_t sigma,
+                     int64_t lambda_num, int64_t lambda_den, int32_t mode,
+                     flexis_support_result *out) {
+    if (!g || !pattern || !out) return FLEXIS_E_INVALID;
+    std::vector<Plan> plans(1);
+    int rc = compile_plan(g->hg, *pattern, sigma, lambda_num, lambda_den, mode, plans[0]);
+    if (rc) return rc;
+    flexis_support_result r;
+    rc = eval_plans(g, plans, &r);
+    if (rc) return rc;
+    *out = r;
+    return FLEXIS_OK;
+}
+
+int flexis_support(flexis_graph *g, const flexis_pattern *pattern, int64_t sigma, double lambda,
+                   int32_t mode, flexis_support_result *out) {
+    int64_t num;
+    if (!lambda_to_q(lambda, &num)) return FLEXIS_E_INVALID;
+    return flexis_support_q(g, pattern, sigma, num, LAMBDA_DEN, mode, out);
+}
+
+int flexis_compile(flexis_graph *g, const flexis_pattern *patterns, const int64_t *sigma,
+                   const int64_t *lambda_num, int64_t lambda_den, int32_t count, int32_t mode,
+                   flexis_plan *plans_out) {
+    if (!g || count < 0 || (count > 0 && (!patterns || !sigma || !lambda_num || !plans_out)))
+        return FLEXIS_E_INVALID;
+    for (int32_t i = 0; i < count; i++) {
+        Plan P;
+        compile_plan(g->hg, patterns[i], sigma[i], lambda_num[i], lambda_den, mode, P);
+        memset(&plans_out[i], 0, sizeof(flexis_plan));
+        memcpy(&plans_out[i], &P, sizeof P);
+    }
+    return FLEXIS_OK;
+}
+
+int flexis_support_batch(flexis_graph *g, const flexis_pattern *patterns, const int64_t *sigma,
+                         const double *lambda, int32_t count, int32_t mode,
+                         flexis_support_result *out) {
+    if (!g || count < 0 || (count > 0 && (!patterns || !sigma || !lambda || !out)))
+        return FLEXIS_E_INVALID;
+    if (count == 0) return FLEXIS_OK;
+    std::vector<Plan> plans((size_t)count);
+    int T = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (count < 256) T = 1;
+    std::vector<std::thread> th;
+    auto work = [&](int t) {
+        for (int32_t i = t; i < count; i += T) {
+            int64_t num = 0;
+            if (!lambda_to_q(lambda[i], &num)) {
+                memset(&plans[(size_t)i], 0, sizeof(Plan));
+                plans[(size_t)i].status = FLEXIS_E_INVALID;
+                plans[(size_t)i].n = patterns[i].n;
+                continue;
+            }
+            compile_plan(g->hg, patterns[i], sigma[i], num, LAMBDA_DEN, mode, plans[(size_t)i]);
+        }
+    };
+    for (int t = 1; t < T; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+    return eval_plans(g, plans, out);
+}
+
+int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int32_t count,
+                                flexis_support_result *d_results, void *stream) {
+    if (!g || count < 0 || (count > 0 && (!d_plans || !d_results))) return FLEXIS_E_INVALID;
+    EvalConfig cfg = config_for(g, count);
+    cudaStream_t s = stream ? (cudaStream_t)stream : dev_graph_stream(g->dg);
+    return dev_eval(g->dg, reinterpret_cast<const Plan *>(d_plans), count, d_results, s, cfg, &g->last);
+}
+
+int flexis_last_stats(const flexis_graph *g, flexis_stats *out) {
+    if (!g || !out) return FLEXIS_E_INVALID;
+    *out = g->last;
+    return FLEXIS_OK;
+}
+
+int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,
+                         int64_t *n_out) {
+    if (!g || !maps_out || !n_out || cap < 0) return FLEXIS_E_INVALID;
+    return dev_selected(g->dg, i, maps_out, cap, n_out);
+}
+
+int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges,
+                flexis_pattern_set **out) {
+    int64_t num;
+    if (!g || !out || sigma < 1 || max_edges < 1 || !lambda_to_q(lambda, &num)) return FLEXIS_E_INVALID;
+    std::unique_ptr<flexis_pattern_set> S(new flexis_pattern_set());
+    S->label_of_rank = g->hg.label_of_rank;
+    // level 2: edges(G), one candidate per label pair on a data edge
+    std::vector<Code> C;
+    for (auto &pr : g->hg.label_pairs) {
+        Code c;
+        c.n = 2;
+        c.lab[0] = pr.first;
+        c.lab[1] = pr.second;
+        c.bits = 0;
+        C.push_back(c);
+    }
+    std::sort(C.begin(), C.end());
+    int threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    for (int k = 2; k <= max_edges + 1 && k <= FLEXIS_MAX_PATTERN && !C.empty(); k++) {
+        S->cand[k] = (int64_t)C.size();
+        std::vector<Plan> plans(C.size());
+        std::vector<int32_t> labels, edges;
+        for (size_t i = 0; i < C.size(); i++) {
+            pattern_of_code(g, C[i], labels, edges);
+            flexis_pattern p{(int32_t)labels.size(), (int32_t)(edges.size() / 2), labels.data(), edges.data()};
+            compile_plan(g->hg, p, sigma, num, LAMBDA_DEN, FLEXIS_MODE_EARLY, plans[i]);
+        }
+        std::vector<flexis_support_result> res(C.size());
+        int rc = eval_plans(g, plans, res.data());
+        if (rc) return rc;
+        std::vector<Code> F;
+        for (size_t i = 0; i < C.size(); i++)
+            if (res[i].status == FLEXIS_OK && res[i].frequent) {
+                F.push_back(C[i]);
+                S->items.push_back({C[i], res[i]});
+            }
+        S->freq[k] = (int64_t)F.size();
+        C.clear();
+        if (k + 1 <= max_edges + 1 && k + 1 <= FLEXIS_MAX_PATTERN) generate_candidates(F, max_edges, C, threads);
+    }
+    *out = S.release();
+    return FLEXIS_OK;
+}
+
+int64_t flexis_pattern_set_count(const flexis_pattern_set *s) { return s ? (int64_t)s->items.size() : 0; }
+
+int flexis_pattern_set_get(const flexis_pattern_set *s, int64_t i, int32_t *n, int32_t *labels,
+                           int32_t *m, int32_t *edges, int32_t *code_labels, uint32_t *code_bits,
+                           flexis_support_result *result) {
+    if (!s || i < 0 || i >= (int64_t)s->items.size()) return FLEXIS_E_INVALID;
+    const auto &e = s->items[(size_t)i];
+    Pat p = pat_of_code(e.code);
+    if (n) *n = p.n;
+    int mm = 0;
+    for (int a = 0; a < p.n; a++) {
+        if (labels) labels[a] = s->label_of_rank[(size_t)p.lab[a]];
+        if (code_labels) code_labels[a] = e.code.lab[a];
+        for (int b = a + 1; b < p.n; b++)
+            if (p.adj[a] >> b & 1) {
+                if (edges) { edges[2 * mm] = a; edges[2 * mm + 1] = b; }
+                mm++;
+            }
+    }
+    if (m) *m = mm;
+    if (code_bits) *code_bits = e.code.bits;
+    if (result) *result = e.res;
+    return FLEXIS_OK;
+}
+
+int flexis_pattern_set_levels(const flexis_pattern_set *s, int64_t *candidates, int64_t *frequent) {
+    if (!s) return FLEXIS_E_INVALID;
+    for (int k = 0; k <= FLEXIS_MAX_PATTERN; k++) {
+        if (candidates) candidates[k] = s->cand[k];
+        if (frequent) frequent[k] = s->freq[k];
+    }
+    return FLEXIS_OK;
+}
+
+void flexis_free_pattern_set(flexis_pattern_set *s) { delete s; }
+
+int flexis_canonical_code(const flexis_pattern *pattern, int32_t *labels_out, uint32_t *bits_out,
+                          int32_t *perm_out) {
+    if (!pattern || !labels_out || !bits_out) return FLEXIS_E_INVALID;
+    if (pattern->n < 1 || pattern->n > MAXN || pattern->m < 0 || !pattern->labels) return FLEXIS_E_INVALID;
+    Pat p;
+    p.n = pattern->n;
+    for (int i = 0; i < p.n; i++) p.lab[i] = pattern->labels[i];
+    for (int e = 0; e < pattern->m; e++) {
+        int a = pattern->edges[2 * e], b = pattern->edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= p.n || b >= p.n || a == b) return FLEXIS_E_INVALID;
+        p.adj[a] |= (uint8_t)(1 << b);
+        p.adj[b] |= (uint8_t)(1 << a);
+    }
+    int perm[MAXN];
+    Code c = canonical(p, perm);
+    for (int i = 0; i < p.n; i++) {
+        labels_out[i] = c.lab[i];
+        if (perm_out) perm_out[i] = perm[i];
+    }
+    *bits_out = c.bits;
+    return FLEXIS_OK;
+}
+
+int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count,
+                                   int32_t max_edges, int32_t *n_out, int32_t *labels_out,
+                                   uint32_t *bits_out, int64_t cap) {
+    if (count < 0 || (count > 0 && !frequent)) return FLEXIS_E_INVALID;
+    std::vector<Code> F;
+    for (int32_t i = 0; i < count; i++) {
+        int32_t lab[MAXN];
+        uint32_t bits;
+        if (flexis_canonical_code(&frequent[i], lab, &bits, nullptr)) return FLEXIS_E_INVALID;
+        Code c;
+        c.n = frequent[i].n;
+        for (int j = 0; j < c.n; j++) c.lab[j] = lab[j];
+        c.bits = bits;
+        F.push_back(c);
+    }
+    std::sort(F.begin(), F.end());
+    F.erase(std::unique(F.begin(), F.end()), F.end());
+    std::vector<Code> C;
+    int threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    generate_candidates(F, max_edges, C, threads);
+    int64_t n = (int64_t)C.size();
+    if (n > cap) return -n;
+    for (int64_t i = 0; i < n; i++) {
+        n_out[i] = C[(size_t)i].n;
+        for (int j = 0; j < MAXN; j++) labels_out[8 * i + j] = j < C[(size_t)i].n ? C[(size_t)i].lab[j] : 0;
+        bits_out[i] = C[(size_t)i].bits;
+    }
+    return n;
+}
+
+
+// ------------------------------------------------------------------ serving
+}  // extern "C"
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+
+struct flexis_server {
+    using clock = std::chrono::steady_clock;
+    struct Req {
+        int64_t id;
+        Plan plan;
+        clock::time_point t0;
+    };
+    struct Done {
+        int64_t id;
+        flexis_support_result res;
+        double lat_us;
+    };
+    flexis_graph *g = nullptr;
+    ServeSession *sess = nullptr;
+    int32_t slots = 0;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    int err = FLEXIS_OK;
+    std::deque<Req> pending;
+    size_t max_pending = 1u << 20;
+    std::deque<Done> done;
+
+    void loop() {
+        std::vector<int64_t> slot_id((size_t)slots, -1);
+        std::vector<clock::time_point> slot_t0((size_t)slots);
+        std::vector<int32_t> phase((size_t)slots, 0), admit;
+        std::vector<Plan> aplans;
+        std::vector<flexis_support_result> res((size_t)slots);
+        int busy = 0;
+        for (;;) {
+            admit.clear();
+            aplans.clear();
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (!stop && busy == 0 && pending.empty())
+                    cv.wait(lk, [&] { return stop || !pending.empty(); });
+                if (stop) break;
+                // admission: a free slot is the unit of device memory (used bitmap + window)
+                for (int32_t i = 0; i < slots && !pending.empty(); i++) {
+                    if (slot_id[(size_t)i] >= 0) continue;
+                    Req r = pending.front();
+                    pending.pop_front();
+                    slot_id[(size_t)i] = r.id;
+                    slot_t0[(size_t)i] = r.t0;
+                    admit.push_back(i);
+                    aplans.push_back(r.plan);
+                    busy++;
+                }
+            }
+            int32_t ng = 0;
+            int rc = serve_step(sess, admit.data(), aplans.data(), (int32_t)admit.size(), phase.data(),
+                                res.data(), &ng);
+            if (rc) {
+                std::lock_guard<std::mutex> lk(mu);
+                err = rc;
+                stop = true;
+                break;
+            }
+            auto now = clock::now();
+            std::lock_guard<std::mutex> lk(mu);
+            for (int32_t i = 0; i < slots; i++) {
+                if (slot_id[(size_t)i] < 0 || phase[(size_t)i] != 3) continue;
+                double us = std::chrono::duration<double, std::micro>(now - slot_t0[(size_t)i]).count();
+                done.push_back(Done{slot_id[(size_t)i], res[(size_t)i], us});
+                slot_id[(size_t)i] = -1;
+                busy--;
+            }
+        }
+    }
+};
+
+extern "C" {
+
+int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out) {
+    if (!g || !out) return FLEXIS_E_INVALID;
+    if (slots <= 0) {
+        // admission by memory: a quarter of the free device memory, in slot units
+        size_t fr = 0, tot = 0;
+        cudaSetDevice(dev_graph_device(g->dg));
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return FLEXIS_E_CUDA;
+        int64_t per = 1;
+        serve_slot_bytes(g->dg, &per);
+        slots = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(fr / 4) / std::max<int64_t>(per, 1)));
+    }
+    std::unique_ptr<flexis_server> s(new flexis_server());
+    s->g = g;
+    s->slots = slots;
+    int rc = serve_create(g->dg, slots, &s->sess);
+    if (rc) return rc;
+    flexis_server *raw = s.get();
+    s->th = std::thread([raw] { raw->loop(); });
+    *out = s.release();
+    return FLEXIS_OK;
+}
+
+int flexis_serve_submit(flexis_server *s, int64_t request_id, const flexis_pattern *pattern,
+                        int64_t sigma, double lambda, int32_t mode) {
+    if (!s || !pattern) return FLEXIS_E_INVALID;
+    int64_t num;
+    if (!lambda_to_q(lambda, &num)) return FLEXIS_E_INVALID;
+    flexis_server::Req r;
+    r.id = request_id;
+    r.t0 = flexis_server::clock::now();
+    int rc = compile_plan(s->g->hg, *pattern, sigma, num, LAMBDA_DEN, mode, r.plan);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->err) return s->err;
+        if (s->stop) return FLEXIS_E_CANCELLED;
+        if (s->pending.size() >= s->max_pending) return FLEXIS_E_BUSY;
+        s->pending.push_back(r);
+    }
+    s->cv.notify_one();
+    return FLEXIS_OK;
+}
+
+int flexis_serve_poll(flexis_server *s, int64_t *ids, flexis_support_result *results,
+                      double *latency_us, int32_t max, int32_t *n_out) {
+    if (!s || !n_out || max < 0 || (max > 0 && (!ids || !results))) return FLEXIS_E_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int32_t k = 0;
+    while (k < max && !s->done.empty()) {
+        auto &d = s->done.front();
+        ids[k] = d.id;
+        results[k] = d.res;
+        if (latency_us) latency_us[k] = d.lat_us;
+        s->done.pop_front();
+        k++;
+    }
+    *n_out = k;
+    return s->err;
+}
+
+int flexis_serve_stop(flexis_server *s) {
+    if (!s) return FLEXIS_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->th.joinable()) s->th.join();
+    int err = s->err;
+    serve_destroy(s->sess);
+    delete s;
+    return err;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal types of the FLEXIS GB300 library (host runtime + kernels).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <array>
+#include <string>
+#include <vector>
+
+#include "../../include/flexis.h"
+
+namespace fx {
+
+constexpr int MAXN = 8;                 // largest pattern (vertices)
+constexpr int64_t CAP_INF = INT64_MAX;  // "no cap" (FULL mode)
+constexpr uint64_t DEFAULT_SEED = 0x5EEDull;
+constexpr uint32_t RUN_SENTINEL_LABEL = 0xFFu;
+
+// A matching order over the canonical pattern (Sec. 3.2.2 matcher, depth-first by level).
+// Level i binds canonical vertex vert[i]; its candidates must carry rank label lab[i], be
+// adjacent to the data vertices bound at every level j with bit j of bmask[i], and differ from
+// those bound at the levels in injmask[i] (earlier levels with the same label).
+struct LevelPlan {
+    uint8_t lab[MAXN];
+    uint8_t bmask[MAXN];
+    uint8_t injmask[MAXN];
+    uint8_t vert[MAXN];
+};
+
+// Compiled pattern (host pattern compiler output; plain bytes, device readable).
+struct Plan {
+    int32_t n;
+    int32_t status;      // FLEXIS_OK or an error for this pattern
+    uint32_t flags;      // FLEXIS_FLAG_*
+    int32_t n_orb;       // automorphism orbits (MNI representatives)
+    int64_t sigma, tau, cap;  // cap: EARLY max(tau,1); FULL CAP_INF
+    int32_t mode;
+    int32_t root_begin, root_end;  // greedy roots: slice of the label index
+    int32_t n_edges;
+    LevelPlan greedy;               // matching order rooted at canonical vertex 0
+    LevelPlan orb[MAXN];            // matching order rooted at each orbit representative
+    int32_t orb_begin[MAXN], orb_end[MAXN];  // candidate slice of the label index per orbit
+    int32_t code_lab[MAXN];         // canonical code: rank labels in canonical order
+    uint32_t code_bits;             // canonical code: adjacency bits
+    int32_t code_n;
+};
+static_assert(sizeof(Plan) <= sizeof(flexis_plan), "plan must fit flexis_plan");
+
+// Per-vertex record, one 16-byte load: adjacency offset, label-run offset, number of runs,
+// rank label.
+struct VRec {
+    uint32_t adj;
+    uint32_t run;
+    uint32_t nrun;
+    uint32_t lab;
+};
+
+// Host copy of the data graph layout (built on the host, mirrored on the device).
+struct HostGraph {
+    int64_t nv = 0;
+    int32_t nl_ids = 0;                 // label ids 0..nl_ids-1
+    int32_t nl = 0;                     // labels present (ranks 0..nl-1)
+    std::vector<int32_t> rank_of;       // [nl_ids] rank or -1
+    std::vector<int32_t> label_of_rank; // [nl]
+    std::vector<VRec> vrec;             // [nv]
+    std::vector<uint32_t> runs;         // per vertex: runs (lab<<24 | rel start) + sentinel
+    std::vector<int32_t> adj;           // sorted by (rank label, id) per vertex
+    std::vector<int32_t> lab_vtx;       // vertices by (rank, H(seed,v), v)
+    std::vector<int32_t> lab_ptr;       // [nl+1]
+    std::vector<std::pair<int32_t, int32_t>> label_pairs;  // rank pairs (a<=b) on data edges
+    int64_t n_arcs = 0;
+    int64_t self_loops = 0, duplicates = 0;
+    int32_t max_degree = 0;
+    uint64_t seed = DEFAULT_SEED;
+};
+
+uint64_t root_hash(uint64_t seed, int64_t r);
+
+// host graph construction (graph.cpp)
+int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
+                     const int32_t *dst, uint64_t seed, HostGraph &out);
+
+// ------------------------------------------------------------------ patterns (pattern.cpp)
+struct Pat {  // small labelled graph, adjacency as bit rows
+    int n = 0;
+    int32_t lab[MAXN] = {0};
+    uint8_t adj[MAXN] = {0};  // bit j of adj[i]: i ~ j
+};
+
+struct Code {  // canonical code: (n, labels, bits)
+    int n = 0;
+    int32_t lab[MAXN] = {0};
+    uint32_t bits = 0;
+    bool operator<(const Code &o) const;
+    bool operator==(const Code &o) const;
+};
+
+struct CodeHash {
+    size_t operator()(const Code &c) const;
+};
+
+// canonical form: returns the code; perm[p] = vertex of `p` at canonical position p
+Code canonical(const Pat &p, int *perm);
+Pat pat_of_code(const Code &c);
+bool connected(const Pat &p);
+int edge_count(const Pat &p);
+// all automorphisms of p (as permutations), capped at `limit`
+void automorphisms(const Pat &p, std::vector<std::array<int8_t, MAXN>> *out, size_t limit);
+// orbit id per vertex (smallest vertex of its orbit)
+void orbits(const Pat &p, int *orb);
+// matching order rooted at `first` over canonical pattern q
+LevelPlan level_plan(const Pat &q, int first);
+
+// pattern compile: labels as graph label ids
+int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, int64_t lam_num,
+                 int64_t lam_den, int mode, Plan &out);
+int64_t tau_exact(int64_t sigma, int64_t lam_num, int64_t lam_den, int n);
+
+// candidate generation (Algorithms 2-4): F given as canonical codes (labels as given)
+void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<Code> &out,
+                         int threads);
+
+}  // namespace fx

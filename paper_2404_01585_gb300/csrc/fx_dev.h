@@ -1,0 +1,51 @@
+// Device side of the FLEXIS GB300 library: resident graph and batched support evaluation.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fx.h"
+
+namespace fx {
+
+struct DeviceGraph;  // resident CSR + label index + per-graph evaluation workspace
+
+struct EvalConfig {
+    int32_t w_min = 32;         // speculation window per pattern (slots), lower bound
+    int32_t w_max = 512;        // upper bound (hash table in shared memory sized for it)
+    int32_t search_blocks = 0;  // 0: SM count x resident blocks per SM
+    int32_t record_selected = 0;
+    int32_t rounds_per_sync = 4;
+    bool timing = false;        // per-launch CUDA events around the search kernel
+};
+
+int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);
+void dev_graph_destroy(DeviceGraph *g);
+int dev_graph_device(const DeviceGraph *g);
+int64_t dev_graph_bytes(const DeviceGraph *g);
+int dev_graph_props(const DeviceGraph *g, int *sm_count, int *l2_bytes);
+cudaStream_t dev_graph_stream(const DeviceGraph *g);
+
+// Evaluate P compiled plans that are already in device memory; results to device memory.
+// Synchronises `stream` before returning.  stats (nullable) receives counters.
+int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_result *d_results,
+             cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats);
+
+// Host-buffer convenience: copy plans in, evaluate, copy results out (on the graph's stream).
+int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support_result *h_results,
+                  const EvalConfig &cfg, flexis_stats *stats);
+
+// Selected maps of pattern i recorded by the last evaluation (cfg.record_selected > 0).
+int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int64_t *n_out);
+
+// Serving session: `slots` pattern slots on the graph's device with their own workspace.
+struct ServeSession;
+int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out);
+void serve_destroy(ServeSession *s);
+// Device bytes one slot holds (used bitmap + window + state); the admission unit.
+int serve_slot_bytes(const DeviceGraph *g, int64_t *bytes);
+// Admit plans into the listed free slots, run one round for every slot in its greedy phase and
+// the MNI search of slots that just finished it.  phase_out[slots]: 0 free, 1 greedy, 2 MNI,
+// 3 ready (res_out[i] then holds slot i's result).  *n_greedy: slots still in greedy phase.
+int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_plans, int32_t n_admit,
+               int32_t *phase_out, flexis_support_result *res_out, int32_t *n_greedy);
+
+}  // namespace fx

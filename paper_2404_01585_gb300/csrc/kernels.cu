@@ -1,0 +1,1094 @@
+// sm_103a kernels of the FLEXIS support-evaluation path and the batched driver.
+//
+// What is computed (per pattern, all integer):
+//   mIS  : the greedy maximal independent set of the pattern's maps (Sec. 2.4.3) taken in the
+//          fixed order (H(seed, root), root, lexicographic tuple in matching order): roots are
+//          visited in hash order, each root selects its lexicographically first map that avoids
+//          vertices already used and then stops (Sec. 3.2.2, changes 1 and 2).  EARLY mode
+//          stops at c = max(tau, 1) selections (Sec. 3.1.1).
+//   MNI  : min over automorphism orbits of the number of distinct data vertices that some map
+//          sends the orbit's vertices to (Sec. 2.4.4).
+//   tau / frequent (Eq. tau).
+//
+// How the sequential greedy is made parallel without changing its result (speculation by
+// windows, per pattern):
+//   * a window holds the next W roots in greedy order; every root in it needing a map gets one
+//     warp that searches its lexicographically first map avoiding the *current* used set
+//     (k_search, warp-cooperative depth-first search over label slices);
+//   * k_commit builds, in shared memory, an inverted index vertex -> smallest window slot whose
+//     map holds it (the owner), finds the first slot f whose map shares a vertex with an
+//     earlier slot's map, and commits every slot before f: each of those maps is the first map
+//     of its root avoiding the vertices of all earlier selections, exactly as in the sequential
+//     greedy.  Slots after f keep their maps unless a committed map took one of their vertices
+//     (a map that avoids a smaller used set and also avoids the larger one is still the first
+//     one: used sets only grow).  Roots without a map are decided at once for the same reason.
+//   * new roots refill the window; the loop ends when c maps are selected or the roots run out.
+// The result is therefore bit-identical to the sequential greedy for any window size, launch
+// shape or batch composition.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fx_dev.h"
+
+namespace fx {
+
+#define FULLMASK 0xFFFFFFFFu
+
+enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2 };
+
+struct DevGraphView {
+    const VRec *vrec;
+    const uint32_t *runs;
+    const int32_t *adj;
+    const int32_t *lab_vtx;
+    int64_t nv;
+    int32_t words;  // used-bitmap words per pattern
+};
+
+// slot phases: free, greedy rounds, MNI pending, result ready
+enum : int32_t { PH_FREE = 0, PH_GREEDY = 1, PH_MNI = 2, PH_READY = 3 };
+
+struct PatState {
+    int64_t count;     // maps selected so far
+    int64_t searched;  // root searches run
+    int32_t cursor;    // next root (index into lab_vtx)
+    int32_t nwin;      // slots in the window
+    int32_t W;         // target window size
+    int32_t done;
+    int32_t exhausted; // every root processed
+    int32_t rounds;
+    int32_t phase;
+    int32_t logged;    // selected maps written to the selection log
+    unsigned long long mni_cnt[MAXN];
+};
+
+struct Ctl {
+    int32_t n_items[2];
+    int32_t next_item[2];
+    int32_t active[2];
+    int32_t err;
+    int32_t pad;
+    unsigned long long bytes_greedy;
+    unsigned long long bytes_mni;
+    unsigned long long search_items;
+    unsigned long long mni_items;
+    unsigned long long mni_total;
+    unsigned long long mni_next;
+};
+
+struct Batch {
+    DevGraphView G;
+    const Plan *plans;
+    int32_t P;
+    int32_t Wmax;
+    int32_t Wmin;
+    int32_t sel_cap;
+    PatState *st;
+    uint32_t *used;       // [P][words]
+    int32_t *win_root;    // [P][Wmax]
+    int32_t *win_state;   // [P][Wmax]
+    int32_t *win_map;     // [P][Wmax][8] (by level)
+    int2 *items;          // [P*Wmax]
+    Ctl *ctl;
+    int32_t *sel;         // [P][sel_cap][8] selected maps, canonical vertex order
+    unsigned long long *mni_seg;  // [P*8+1] prefix sums of MNI candidate segments
+    flexis_support_result *results;
+};
+
+// ------------------------------------------------------------------ warp depth-first search
+struct WarpState {
+    int32_t t[MAXN];                    // data vertex bound at each level
+    uint32_t lo[MAXN], hi[MAXN];        // driver slice of each level
+    uint32_t pos[MAXN], base[MAXN], mask[MAXN];
+    uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
+    int32_t nchk[MAXN];
+    LevelPlan L;
+    int32_t n;
+    int32_t pad[3];
+};
+
+__device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
+    return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Slice of v's neighbours carrying rank label `lab` (warp-cooperative: one load of up to 32
+// label runs, ballot on the label).  Returns an empty slice when the label is absent.
+__device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uint32_t lab,
+                                           uint32_t &lo, uint32_t &hi, unsigned long long &bytes) {
+    const int lane = threadIdx.x & 31;
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec) + v);
+    bytes += 16;
+    const uint32_t adj = r.x, run = r.y, nrun = r.z;
+    lo = hi = 0;
+    for (uint32_t j0 = 0; j0 < nrun; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t e = (j <= nrun) ? __ldg(G.runs + run + j) : 0xFFFFFFFFu;
+        const uint32_t nx = __shfl_down_sync(FULLMASK, e, 1);
+        bytes += 4ull * min(32u, nrun + 1 - j0);
+        const bool hit = (j < nrun) && ((e >> 24) == lab);
+        const unsigned b = __ballot_sync(FULLMASK, hit);
+        if (b) {
+            const int s = __ffs(b) - 1;
+            const uint32_t es = __shfl_sync(FULLMASK, e, s);
+            uint32_t en = __shfl_sync(FULLMASK, nx, s);
+            if (s == 31) en = __ldg(G.runs + run + j0 + 32);
+            lo = adj + (es & 0xFFFFFFu);
+            hi = adj + (en & 0xFFFFFFu);
+            return;
+        }
+        const uint32_t last = __shfl_sync(FULLMASK, e, 31);
+        if ((last >> 24) > lab) return;  // runs are sorted by label
+    }
+}
+
+__device__ __forceinline__ bool contains(const int32_t *adj, uint32_t lo, uint32_t hi, int32_t c,
+                                         uint32_t &probes) {
+    uint32_t a = lo, b = hi;
+    while (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        probes++;
+        if (__ldg(adj + m) < c) a = m + 1; else b = m;
+    }
+    if (a >= hi) return false;
+    probes++;
+    return __ldg(adj + a) == c;
+}
+
+// Prepare level i: slices of the bound neighbours at every backward level; the shortest one
+// drives the scan, the others are membership tests.  False if some slice is empty.
+__device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W, int i,
+                                            unsigned long long &bytes) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lab = W.L.lab[i];
+    uint32_t bm = W.L.bmask[i];
+    uint32_t dlo = 0, dhi = 0, dlen = 0xFFFFFFFFu;
+    int nchk = 0;
+    while (bm) {
+        const int b = __ffs(bm) - 1;
+        bm &= bm - 1;
+        uint32_t lo, hi;
+        find_slice(G, W.t[b], lab, lo, hi, bytes);
+        if (lo == hi) return false;
+        const uint32_t len = hi - lo;
+        if (len < dlen) {
+            if (dlen != 0xFFFFFFFFu) {
+                if (lane == 0) { W.clo[i][nchk] = dlo; W.chi[i][nchk] = dhi; }
+                nchk++;
+            }
+            dlo = lo; dhi = hi; dlen = len;
+        } else {
+            if (lane == 0) { W.clo[i][nchk] = lo; W.chi[i][nchk] = hi; }
+            nchk++;
+        }
+    }
+    if (lane == 0) { W.lo[i] = dlo; W.hi[i] = dhi; W.nchk[i] = nchk; }
+    __syncwarp();
+    return true;
+}
+
+__device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
+                                                int32_t c, const uint32_t *used,
+                                                uint32_t &probes) {
+    uint32_t im = W.L.injmask[i];
+    while (im) {
+        const int b = __ffs(im) - 1;
+        im &= im - 1;
+        if (W.t[b] == c) return false;
+    }
+    if (used) {
+        probes++;
+        if (used_bit(used, c)) return false;
+    }
+    const int nchk = W.nchk[i];
+    for (int k = 0; k < nchk; k++)
+        if (!contains(G.adj, W.clo[i][k], W.chi[i][k], c, probes)) return false;
+    return true;
+}
+
+// Lexicographically first map (in the level order of W.L) with level 0 bound to `root` and no
+// vertex in `used` (nullable).  On success W.t holds the map by level.
+__device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
+                          unsigned long long &bytes, uint32_t &probes) {
+    const int lane = threadIdx.x & 31;
+    const int n = W.n;
+    if (lane == 0) W.t[0] = root;
+    __syncwarp();
+    if (used) {
+        bytes += 4;
+        if (used_bit(used, root)) return false;
+    }
+    int i = 1;
+    bool ok = enter_level(G, W, 1, bytes);
+    uint32_t hi = 0, pos = 0, base = 0, mask = 0;
+    if (ok) { hi = W.hi[1]; pos = W.lo[1]; }
+    for (;;) {
+        if (!ok) {
+            if (--i == 0) return false;
+            hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i];
+            ok = true;
+            continue;
+        }
+        if (mask == 0) {
+            if (pos >= hi) { ok = false; continue; }
+            const uint32_t k = pos + lane;
+            bool good = false;
+            if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes);
+            mask = __ballot_sync(FULLMASK, good);
+            bytes += 4ull * min(32u, hi - pos);
+            base = pos;
+            pos += 32;
+            continue;
+        }
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int32_t c = __ldg(G.adj + base + j);
+        if (lane == 0) W.t[i] = c;
+        if (i == n - 1) { __syncwarp(); return true; }
+        if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; }
+        __syncwarp();
+        ++i;
+        ok = enter_level(G, W, i, bytes);
+        if (ok) { hi = W.hi[i]; pos = W.lo[i]; mask = 0; }
+    }
+}
+
+__device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, int n) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 8) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
+    if (lane == 0) W.n = n;
+    __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ kernels
+constexpr int SEARCH_THREADS = 256;
+constexpr int COMMIT_THREADS = 256;
+
+__device__ void reset_ctl(Ctl *c) {
+    c->n_items[0] = c->n_items[1] = 0;
+    c->next_item[0] = c->next_item[1] = 0;
+    c->active[0] = c->active[1] = 0;
+    c->err = 0;
+    c->bytes_greedy = c->bytes_mni = 0;
+    c->search_items = c->mni_items = 0;
+    c->mni_total = c->mni_next = 0;
+}
+
+__device__ void init_slot(const Batch &B, int p) {
+    const Plan &P = B.plans[p];
+    PatState s;
+    memset(&s, 0, sizeof s);
+    s.cursor = P.root_begin;
+    s.W = B.Wmin;
+    const bool nothing = P.status != FLEXIS_OK || (P.flags & FLEXIS_FLAG_ABSENT_LABEL) ||
+                         P.root_begin >= P.root_end;
+    s.done = nothing ? 1 : 0;
+    s.exhausted = nothing ? 1 : 0;
+    s.phase = nothing ? PH_MNI : PH_GREEDY;
+    B.st[p] = s;
+}
+
+// closed batch: every slot [0, P) starts
+__global__ void k_init(Batch B) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) reset_ctl(B.ctl);
+    if (p < B.P) init_slot(B, p);
+}
+
+// serving: (re)start the listed slots and clear their used bitmaps; one block per slot
+__global__ void k_admit(Batch B, const int32_t *slots, int n) {
+    if (blockIdx.x >= n) return;
+    const int p = slots[blockIdx.x];
+    uint32_t *u = B.used + (size_t)p * B.G.words;
+    for (int w = threadIdx.x; w < B.G.words; w += blockDim.x) u[w] = 0;
+    if (threadIdx.x == 0) init_slot(B, p);
+}
+
+__global__ void k_reset_ctl(Batch B) { reset_ctl(B.ctl); }
+
+// One warp per (pattern, slot) item: first map of the slot's root avoiding the used set.
+__global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch B, int q) {
+    __shared__ WarpState ws[SEARCH_THREADS / 32];
+    const int lane = threadIdx.x & 31;
+    WarpState &W = ws[threadIdx.x >> 5];
+    const int n_items = *reinterpret_cast<volatile int32_t *>(&B.ctl->n_items[q]);
+    unsigned long long bytes = 0;
+    uint32_t probes = 0;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&B.ctl->next_item[q], 1);
+        it = __shfl_sync(FULLMASK, it, 0);
+        if (it >= n_items) break;
+        const int2 item = B.items[it];
+        const int p = item.x, s = item.y;
+        const Plan &P = B.plans[p];
+        load_level_plan(W, P.greedy, P.n);
+        const size_t slot = (size_t)p * B.Wmax + s;
+        const int32_t root = B.win_root[slot];
+        const bool found = dfs_first(B.G, W, B.used + (size_t)p * B.G.words, root, bytes, probes);
+        if (lane == 0) B.win_state[slot] = found ? SLOT_MAP : SLOT_NONE;
+        if (found && lane < P.n) B.win_map[slot * MAXN + lane] = W.t[lane];
+        __syncwarp();
+    }
+    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
+    if (lane == 0 && tot) atomicAdd(&B.ctl->bytes_greedy, tot);
+}
+
+// Block-wide exclusive scan of one int per thread; returns the total.
+__device__ __forceinline__ int block_scan(int v, int &excl, int *sh /* >= 33 ints */) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULLMASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULLMASK, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) sh[lane] = t;  // inclusive prefix of warp totals
+        if (lane == nw - 1) sh[32] = t;
+    }
+    __syncthreads();
+    excl = x - v + (w > 0 ? sh[w - 1] : 0);
+    const int total = sh[32];
+    __syncthreads();
+    return total;
+}
+
+// hash-table capacity of the commit kernel: a power of two >= 2 x (window slots x 8 vertices)
+__host__ __device__ __forceinline__ int hash_slots(int Wmax) {
+    int t = 64;
+    while (t < 2 * Wmax * MAXN) t <<= 1;
+    return t;
+}
+
+__device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
+    return ((uint32_t)v * 0x9E3779B1u) >> (32 - logT);
+}
+
+// One block per pattern: inverted index of the window's maps, prefix commit, refill, new items.
+__global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
+    extern __shared__ int32_t smem[];
+    __shared__ int sh_scan[40];
+    __shared__ int s_f, s_newcur;
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (p == 0 && tid == 0) {
+        B.ctl->n_items[q ^ 1] = 0;
+        B.ctl->next_item[q ^ 1] = 0;
+        B.ctl->active[q ^ 1] = 0;
+    }
+    PatState *S = B.st + p;
+    if (S->phase != PH_GREEDY) return;
+    const Plan &P = B.plans[p];
+    const int n = P.n;
+    const int nwin = S->nwin;
+    const int Wmax = B.Wmax;
+    const size_t wbase = (size_t)p * Wmax;
+    uint32_t *used = B.used + (size_t)p * B.G.words;
+
+    // shared layout: keys[T] vals[T] | st_root[Wmax] st_state[Wmax] st_map[Wmax*8]
+    int logT = 6;
+    while ((1 << logT) < 2 * nwin * n) logT++;
+    const int T = 1 << logT;
+    const int Tmax = hash_slots(Wmax);
+    int32_t *keys = smem, *vals = smem + Tmax;
+    int32_t *st_root = smem + 2 * Tmax, *st_state = st_root + Wmax, *st_map = st_state + Wmax;
+
+    for (int k = tid; k < T; k += blockDim.x) { keys[k] = -1; vals[k] = INT_MAX; }
+    if (tid == 0) { s_f = nwin; }
+    __syncthreads();
+    // 1. inverted index: vertex -> owner (smallest slot whose map holds it)
+    for (int idx = tid; idx < nwin * n; idx += blockDim.x) {
+        const int s = idx / n, k = idx - s * n;
+        if (B.win_state[wbase + s] != SLOT_MAP) continue;
+        const int32_t v = B.win_map[(wbase + s) * MAXN + k];
+        uint32_t h = hslot(v, logT);
+        for (;;) {
+            const int32_t prev = atomicCAS(&keys[h], -1, v);
+            if (prev == -1 || prev == v) { atomicMin(&vals[h], s); break; }
+            h = (h + 1) & (T - 1);
+        }
+    }
+    __syncthreads();
+    // owner lookup (the vertex is present)
+    auto owner = [&](int32_t v) {
+        uint32_t h = hslot(v, logT);
+        while (keys[h] != v) h = (h + 1) & (T - 1);
+        return vals[h];
+    };
+    // 2. first slot whose map meets an earlier slot's map
+    for (int idx = tid; idx < nwin * n; idx += blockDim.x) {
+        const int s = idx / n, k = idx - s * n;
+        if (B.win_state[wbase + s] != SLOT_MAP) continue;
+        if (owner(B.win_map[(wbase + s) * MAXN + k]) < s) atomicMin(&s_f, s);
+    }
+    __syncthreads();
+    const int f = s_f;
+    // 3. commit the map slots before f, in slot order
+    int64_t count0 = S->count;
+    int ncommit = 0;
+    {
+        const int per = (nwin + blockDim.x - 1) / blockDim.x;
+        int mine = 0;
+        for (int k = 0; k < per; k++) {
+            const int s = tid * per + k;
+            if (s < nwin && s < f && B.win_state[wbase + s] == SLOT_MAP) mine++;
+        }
+        int excl;
+        ncommit = block_scan(mine, excl, sh_scan);
+        int r = excl;
+        for (int k = 0; k < per; k++) {
+            const int s = tid * per + k;
+            if (!(s < nwin && s < f && B.win_state[wbase + s] == SLOT_MAP)) continue;
+            const int32_t *m = B.win_map + (wbase + s) * MAXN;
+            for (int l = 0; l < n; l++) atomicOr(used + (m[l] >> 5), 1u << (m[l] & 31));
+            const int64_t at = count0 + r;
+            if (B.sel && at < B.sel_cap && at < P.cap) {
+                int32_t *o = B.sel + ((size_t)p * B.sel_cap + at) * MAXN;
+                for (int l = 0; l < n; l++) o[P.greedy.vert[l]] = m[l];
+            }
+            r++;
+        }
+    }
+    // 4. keep the slots from f on that still matter; a kept map needs a new search if a
+    //    committed map took one of its vertices
+    int keep_n;
+    {
+        const int per = (nwin + blockDim.x - 1) / blockDim.x;
+        int mine = 0;
+        int flag[8];
+        for (int k = 0; k < per && k < 8; k++) {
+            const int s = tid * per + k;
+            flag[k] = (s < nwin && s >= f && B.win_state[wbase + s] != SLOT_NONE) ? 1 : 0;
+            mine += flag[k];
+        }
+        int excl;
+        keep_n = block_scan(mine, excl, sh_scan);
+        int r = excl;
+        for (int k = 0; k < per && k < 8; k++) {
+            if (!flag[k]) continue;
+            const int s = tid * per + k;
+            int state = B.win_state[wbase + s];
+            if (state == SLOT_MAP) {
+                const int32_t *m = B.win_map + (wbase + s) * MAXN;
+                for (int l = 0; l < n; l++)
+                    if (owner(m[l]) < f) { state = SLOT_NEEDS; break; }
+                for (int l = 0; l < MAXN; l++) st_map[r * MAXN + l] = m[l];
+            }
+            st_root[r] = B.win_root[wbase + s];
+            st_state[r] = state;
+            r++;
+        }
+    }
+    __syncthreads();
+    for (int s = tid; s < keep_n; s += blockDim.x) {
+        B.win_root[wbase + s] = st_root[s];
+        B.win_state[wbase + s] = st_state[s];
+        for (int l = 0; l < MAXN; l++) B.win_map[(wbase + s) * MAXN + l] = st_map[s * MAXN + l];
+    }
+    // 5. window size: grow while speculation is conflict-free
+    int W = S->W;
+    if (nwin > 0 && f >= nwin) W = min(2 * W, Wmax);
+    // 6. refill from the root order, skipping roots already used
+    int nw = keep_n;
+    int cursor = S->cursor;
+    const int rend = P.root_end;
+    __syncthreads();
+    while (nw < W && cursor < rend) {
+        const int chunk = min((int)blockDim.x, rend - cursor);
+        const int need = W - nw;
+        int ok = 0;
+        int32_t r = -1;
+        if (tid < chunk) {
+            r = __ldg(B.G.lab_vtx + cursor + tid);
+            ok = used_bit(used, r) ? 0 : 1;
+        }
+        if (tid == 0) { s_newcur = cursor + chunk; }
+        __syncthreads();
+        int excl;
+        const int tot = block_scan(ok, excl, sh_scan);
+        if (ok && excl < need) {
+            B.win_root[wbase + nw + excl] = r;
+            B.win_state[wbase + nw + excl] = SLOT_NEEDS;
+            if (excl == need - 1) s_newcur = cursor + tid + 1;
+        }
+        __syncthreads();
+        nw += min(tot, need);
+        cursor = s_newcur;
+        __syncthreads();
+    }
+    // 7. emit search items for every slot that needs a map
+    {
+        const int per = (nw + blockDim.x - 1) / blockDim.x;
+        int mine = 0;
+        for (int k = 0; k < per; k++) {
+            const int s = tid * per + k;
+            if (s < nw && B.win_state[wbase + s] == SLOT_NEEDS) mine++;
+        }
+        __syncthreads();
+        int excl;
+        const int tot = block_scan(mine, excl, sh_scan);
+        __shared__ int s_base;
+        if (tid == 0) s_base = tot ? atomicAdd(&B.ctl->n_items[q], tot) : 0;
+        __syncthreads();
+        int r = s_base + excl;
+        for (int k = 0; k < per; k++) {
+            const int s = tid * per + k;
+            if (s < nw && B.win_state[wbase + s] == SLOT_NEEDS) B.items[r++] = make_int2(p, s);
+        }
+        if (tid == 0) {
+            const int64_t count = count0 + ncommit;
+            S->count = count;
+            if (B.sel) S->logged = (int32_t)min(min(count, P.cap), (int64_t)B.sel_cap);
+            S->cursor = cursor;
+            S->nwin = nw;
+            S->W = W;
+            S->rounds++;
+            S->searched += tot;
+            const bool reached = count >= P.cap;
+            const bool exhausted = nw == 0 && cursor >= rend;
+            if (reached || exhausted) {
+                S->done = 1;
+                S->exhausted = exhausted && !reached;
+                S->phase = PH_MNI;
+            } else {
+                atomicAdd(&B.ctl->active[q], 1);
+            }
+            if (tot) atomicAdd(&B.ctl->search_items, (unsigned long long)tot);
+        }
+    }
+}
+
+// MNI segments: for every pattern whose mIS stayed below c and is not zero, one segment per
+// orbit covering the orbit label's vertices.
+__global__ void k_mni_setup(Batch B) {
+    __shared__ int sh[40];
+    __shared__ unsigned long long carry;
+    const int tid = threadIdx.x;
+    const int nseg = B.P * MAXN;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nseg; base += blockDim.x) {
+        const int sidx = base + tid;
+        int len = 0;
+        if (sidx < nseg) {
+            const int p = sidx / MAXN, o = sidx % MAXN;
+            const Plan &P = B.plans[p];
+            const PatState &S = B.st[p];
+            const bool need = S.phase == PH_MNI && P.status == FLEXIS_OK &&
+                              !(P.flags & FLEXIS_FLAG_ABSENT_LABEL) && S.count < P.cap && S.count > 0;
+            if (need && o < P.n_orb) len = P.orb_end[o] - P.orb_begin[o];
+        }
+        int excl;
+        const int tot = block_scan(len, excl, sh);
+        if (sidx < nseg) B.mni_seg[sidx] = carry + (unsigned long long)excl;
+        __syncthreads();
+        if (tid == 0) carry += (unsigned long long)tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        B.mni_seg[nseg] = carry;
+        B.ctl->mni_total = carry;
+        B.ctl->mni_next = 0;
+    }
+}
+
+constexpr int MNI_CHUNK = 8;
+
+// One warp per candidate vertex d of an orbit: does some map send the orbit representative to d?
+__global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
+    __shared__ WarpState ws[SEARCH_THREADS / 32];
+    const int lane = threadIdx.x & 31;
+    WarpState &W = ws[threadIdx.x >> 5];
+    const unsigned long long total = *reinterpret_cast<volatile unsigned long long *>(&B.ctl->mni_total);
+    const int nseg = B.P * MAXN;
+    unsigned long long bytes = 0, items = 0;
+    uint32_t probes = 0;
+    int cur_seg = -1;
+    for (;;) {
+        unsigned long long c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&B.ctl->mni_next, (unsigned long long)MNI_CHUNK);
+        c0 = __shfl_sync(FULLMASK, c0, 0);
+        if (c0 >= total) break;
+        const unsigned long long c1 = min(total, c0 + MNI_CHUNK);
+        for (unsigned long long c = c0; c < c1; c++) {
+            // segment holding c: last seg with mni_seg[seg] <= c (and non-empty)
+            int lo = 0, hi = nseg;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (B.mni_seg[mid] <= c) lo = mid; else hi = mid;
+            }
+            const int seg = lo;
+            const int p = seg / MAXN, o = seg % MAXN;
+            const Plan &P = B.plans[p];
+            unsigned long long *cnt = &B.st[p].mni_cnt[o];
+            if ((long long)__ldcg(cnt) >= P.cap) continue;
+            if (seg != cur_seg) {
+                load_level_plan(W, P.orb[o], P.n);
+                cur_seg = seg;
+            }
+            const int32_t d = __ldg(B.G.lab_vtx + P.orb_begin[o] + (int)(c - B.mni_seg[seg]));
+            items++;
+            const bool found = dfs_first(B.G, W, nullptr, d, bytes, probes);
+            if (found && lane == 0) atomicAdd(cnt, 1ull);
+        }
+    }
+    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
+    if (lane == 0) {
+        if (tot) atomicAdd(&B.ctl->bytes_mni, tot);
+        if (items) atomicAdd(&B.ctl->mni_items, items);
+    }
+}
+
+__global__ void k_finalize(Batch B) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= B.P) return;
+    const Plan &P = B.plans[p];
+    PatState &S = B.st[p];
+    if (S.phase != PH_MNI) return;
+    S.phase = PH_READY;
+    flexis_support_result r;
+    memset(&r, 0, sizeof r);
+    r.status = P.status;
+    r.n = P.n;
+    r.sigma = P.sigma;
+    r.tau = P.tau;
+    r.cap = P.mode == FLEXIS_MODE_EARLY ? P.cap : -1;
+    r.flags = P.flags;
+    r.roots_searched = S.searched;
+    if (P.status == FLEXIS_OK) {
+        const int64_t cap = P.cap;
+        const int64_t mis = S.count < cap ? S.count : cap;
+        int64_t mni;
+        if (P.flags & FLEXIS_FLAG_ABSENT_LABEL) {
+            mni = 0;
+        } else if (S.count >= cap || S.count == 0) {
+            mni = S.count >= cap ? cap : 0;
+            r.flags |= FLEXIS_FLAG_MNI_FROM_MIS;
+        } else {
+            mni = cap;
+            for (int o = 0; o < P.n_orb; o++) {
+                const int64_t c = (int64_t)S.mni_cnt[o];
+                mni = min(mni, min(c, cap));
+            }
+        }
+        r.mis = mis;
+        r.mni = mni;
+        const int64_t c = P.tau > 1 ? P.tau : 1;
+        r.frequent = mis >= c ? 1 : 0;
+    }
+    B.results[p] = r;
+}
+
+// ------------------------------------------------------------------ device graph + workspaces
+#define CK(x)                                                                         \
+    do {                                                                              \
+        cudaError_t e_ = (x);                                                         \
+        if (e_ != cudaSuccess) {                                                      \
+            fprintf(stderr, "flexis: %s failed: %s\n", #x, cudaGetErrorString(e_));  \
+            return e_ == cudaErrorMemoryAllocation ? FLEXIS_E_NOMEM : FLEXIS_E_CUDA;  \
+        }                                                                             \
+    } while (0)
+
+// Evaluation workspace: P pattern slots with their used bitmaps, windows and work items.
+struct Workspace {
+    int32_t P = 0, W = 0, sel = 0;
+    PatState *st = nullptr;
+    uint32_t *used = nullptr;
+    int32_t *win_root = nullptr, *win_state = nullptr, *win_map = nullptr;
+    int2 *items = nullptr;
+    Ctl *ctl = nullptr;
+    int32_t *sel_buf = nullptr;
+    unsigned long long *mni_seg = nullptr;
+    Plan *plans = nullptr;                   // device plan array (host-plan entry points)
+    flexis_support_result *results = nullptr;
+    int32_t plans_cap = 0;
+    Ctl *h_ctl = nullptr;                    // pinned
+};
+
+struct DeviceGraph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevGraphView view{};
+    void *d_vrec = nullptr, *d_runs = nullptr, *d_adj = nullptr, *d_labvtx = nullptr;
+    int64_t bytes = 0;
+    int sm_count = 0, l2 = 0;
+    Workspace ws;
+    int32_t last_P = 0, last_sel = 0;
+    cudaEvent_t ev[2]{};
+    std::vector<cudaEvent_t> sev;
+};
+
+template <class T>
+static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &bytes) {
+    size_t b = std::max<size_t>(h.size(), 1) * sizeof(T);
+    CK(cudaMalloc(d, b));
+    CK(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    bytes += (int64_t)b;
+    return FLEXIS_OK;
+}
+
+static size_t commit_smem(int Wmax) {
+    return sizeof(int32_t) * ((size_t)2 * hash_slots(Wmax) + (size_t)Wmax * (2 + MAXN));
+}
+
+int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) return FLEXIS_E_CUDA;
+    DeviceGraph *g = new DeviceGraph();
+    g->device = device;
+    int rc = FLEXIS_OK;
+    auto fail = [&](int code) { dev_graph_destroy(g); return code; };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(FLEXIS_E_CUDA);
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FLEXIS_E_CUDA);
+    if ((rc = upload(&g->d_vrec, hg.vrec, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_runs, hg.runs, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_adj, hg.adj, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_labvtx, hg.lab_vtx, g->stream, g->bytes))) return fail(rc);
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(FLEXIS_E_CUDA);
+    g->view.vrec = (const VRec *)g->d_vrec;
+    g->view.runs = (const uint32_t *)g->d_runs;
+    g->view.adj = (const int32_t *)g->d_adj;
+    g->view.lab_vtx = (const int32_t *)g->d_labvtx;
+    g->view.nv = hg.nv;
+    g->view.words = (int32_t)std::max<int64_t>(1, (hg.nv + 31) / 32);
+    if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
+        cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)
+        return fail(FLEXIS_E_CUDA);
+    if (cudaFuncSetAttribute(k_commit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)commit_smem(1024)) != cudaSuccess)
+        return fail(FLEXIS_E_CUDA);
+    *out = g;
+    return FLEXIS_OK;
+}
+
+static void ws_free(Workspace &w) {
+    cudaFree(w.st); cudaFree(w.used); cudaFree(w.win_root); cudaFree(w.win_state);
+    cudaFree(w.win_map); cudaFree(w.items); cudaFree(w.ctl); cudaFree(w.sel_buf);
+    cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results);
+    if (w.h_ctl) cudaFreeHost(w.h_ctl);
+    w = Workspace();
+}
+
+static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax, int32_t sel) {
+    if (P <= w.P && Wmax <= w.W && sel <= w.sel && w.h_ctl) return FLEXIS_OK;
+    const int32_t nP = std::max(P, w.P), nW = std::max(Wmax, w.W), nS = std::max(sel, w.sel);
+    ws_free(w);
+    const size_t words = (size_t)g->view.words;
+    CK(cudaMalloc(&w.st, sizeof(PatState) * nP));
+    CK(cudaMemset(w.st, 0, sizeof(PatState) * nP));
+    CK(cudaMalloc(&w.used, sizeof(uint32_t) * words * nP));
+    CK(cudaMalloc(&w.win_root, sizeof(int32_t) * (size_t)nP * nW));
+    CK(cudaMalloc(&w.win_state, sizeof(int32_t) * (size_t)nP * nW));
+    CK(cudaMalloc(&w.win_map, sizeof(int32_t) * (size_t)nP * nW * MAXN));
+    CK(cudaMalloc(&w.items, sizeof(int2) * (size_t)nP * nW));
+    CK(cudaMalloc(&w.ctl, sizeof(Ctl)));
+    CK(cudaMalloc(&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
+    CK(cudaMalloc(&w.plans, sizeof(Plan) * (size_t)nP));
+    CK(cudaMalloc(&w.results, sizeof(flexis_support_result) * (size_t)nP));
+    if (nS > 0) CK(cudaMalloc(&w.sel_buf, sizeof(int32_t) * (size_t)nP * nS * MAXN));
+    CK(cudaMallocHost((void **)&w.h_ctl, sizeof(Ctl)));
+    w.P = nP;
+    w.W = nW;
+    w.sel = nS;
+    return FLEXIS_OK;
+}
+
+void dev_graph_destroy(DeviceGraph *g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    ws_free(g->ws);
+    cudaFree(g->d_vrec); cudaFree(g->d_runs); cudaFree(g->d_adj); cudaFree(g->d_labvtx);
+    if (g->ev[0]) cudaEventDestroy(g->ev[0]);
+    if (g->ev[1]) cudaEventDestroy(g->ev[1]);
+    for (auto e : g->sev) cudaEventDestroy(e);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+int dev_graph_device(const DeviceGraph *g) { return g->device; }
+int64_t dev_graph_bytes(const DeviceGraph *g) { return g->bytes; }
+cudaStream_t dev_graph_stream(const DeviceGraph *g) { return g->stream; }
+int dev_graph_props(const DeviceGraph *g, int *sm, int *l2) {
+    *sm = g->sm_count;
+    *l2 = g->l2;
+    return FLEXIS_OK;
+}
+
+static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *plans, int32_t P,
+                        int Wmin, int Wmax, int sel, flexis_support_result *results) {
+    Batch B;
+    B.G = g->view;
+    B.plans = plans;
+    B.P = P;
+    B.Wmax = Wmax;
+    B.Wmin = Wmin;
+    B.sel_cap = sel;
+    B.st = w.st;
+    B.used = w.used;
+    B.win_root = w.win_root;
+    B.win_state = w.win_state;
+    B.win_map = w.win_map;
+    B.items = w.items;
+    B.ctl = w.ctl;
+    B.sel = sel > 0 ? w.sel_buf : nullptr;
+    B.mni_seg = w.mni_seg;
+    B.results = results;
+    return B;
+}
+
+static int search_grid(const DeviceGraph *g, const EvalConfig &cfg) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, SEARCH_THREADS, 0) != cudaSuccess)
+        per_sm = 1;
+    return cfg.search_blocks > 0 ? cfg.search_blocks : g->sm_count * std::max(1, per_sm);
+}
+
+int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_result *d_results,
+             cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats) {
+    if (P <= 0) return FLEXIS_OK;
+    CK(cudaSetDevice(g->device));
+    const int Wmax = std::max(32, std::min(cfg.w_max, 1024));
+    const int Wmin = std::max(1, std::min(cfg.w_min, Wmax));
+    int rc = ws_ensure(g, g->ws, P, Wmax, cfg.record_selected);
+    if (rc) return rc;
+    Workspace &w = g->ws;
+    g->last_P = P;
+    g->last_sel = cfg.record_selected;
+    Batch B = make_batch(g, w, d_plans, P, Wmin, Wmax, cfg.record_selected, d_results);
+    const size_t smem = commit_smem(Wmax);
+    const int sblocks = search_grid(g, cfg);
+
+    int64_t launches = 0;
+    CK(cudaEventRecord(g->ev[0], stream));
+    CK(cudaMemsetAsync(w.used, 0, sizeof(uint32_t) * (size_t)g->view.words * P, stream));
+    k_init<<<(P + 255) / 256, 256, 0, stream>>>(B);
+    launches += 1;
+    int64_t rounds = 0;
+    int search_launches = 0;
+    const int R = std::max(1, cfg.rounds_per_sync);
+    size_t evi = 0;
+    for (;;) {
+        for (int r = 0; r < R; r++) {
+            const int q = (int)(rounds & 1);
+            k_commit<<<P, COMMIT_THREADS, smem, stream>>>(B, q);
+            if (cfg.timing) {
+                while (evi + 2 > g->sev.size()) {
+                    cudaEvent_t e;
+                    CK(cudaEventCreate(&e));
+                    g->sev.push_back(e);
+                }
+                CK(cudaEventRecord(g->sev[evi], stream));
+            }
+            k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+            if (cfg.timing) {
+                CK(cudaEventRecord(g->sev[evi + 1], stream));
+                evi += 2;
+            }
+            launches += 2;
+            search_launches++;
+            rounds++;
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (w.h_ctl->active[(rounds - 1) & 1] == 0) break;
+    }
+    cudaEvent_t m0 = nullptr, m1 = nullptr;
+    if (cfg.timing) {
+        CK(cudaEventCreate(&m0));
+        CK(cudaEventCreate(&m1));
+    }
+    k_mni_setup<<<1, 1024, 0, stream>>>(B);
+    if (cfg.timing) CK(cudaEventRecord(m0, stream));
+    k_mni<<<sblocks, SEARCH_THREADS, 0, stream>>>(B);
+    if (cfg.timing) CK(cudaEventRecord(m1, stream));
+    k_finalize<<<(P + 255) / 256, 256, 0, stream>>>(B);
+    launches += 3;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(g->ev[1], stream));
+    CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->rounds = rounds;
+        stats->search_items = (int64_t)w.h_ctl->search_items;
+        stats->mni_items = (int64_t)w.h_ctl->mni_items;
+        stats->kernel_launches = launches;
+        stats->alg_bytes_greedy = (int64_t)w.h_ctl->bytes_greedy;
+        stats->alg_bytes = (int64_t)(w.h_ctl->bytes_greedy + w.h_ctl->bytes_mni);
+        stats->search_launches = search_launches;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g->ev[0], g->ev[1]);
+        stats->total_ms = t;
+        if (cfg.timing) {
+            float sum = 0.f;
+            for (size_t k = 0; k < evi; k += 2) {
+                float x = 0.f;
+                cudaEventElapsedTime(&x, g->sev[k], g->sev[k + 1]);
+                sum += x;
+            }
+            stats->search_ms = sum;
+            float y = 0.f;
+            cudaEventElapsedTime(&y, m0, m1);
+            stats->mni_ms = y;
+        }
+    }
+    if (m0) cudaEventDestroy(m0);
+    if (m1) cudaEventDestroy(m1);
+    return FLEXIS_OK;
+}
+
+int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support_result *h_results,
+                  const EvalConfig &cfg, flexis_stats *stats) {
+    if (P <= 0) return FLEXIS_OK;
+    CK(cudaSetDevice(g->device));
+    Workspace &w = g->ws;
+    int rc = ws_ensure(g, w, P, std::max(32, std::min(cfg.w_max, 1024)), cfg.record_selected);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(w.plans, h_plans, sizeof(Plan) * (size_t)P, cudaMemcpyHostToDevice, g->stream));
+    rc = dev_eval(g, w.plans, P, w.results, g->stream, cfg, stats);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h_results, w.results, sizeof(flexis_support_result) * (size_t)P,
+                       cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return FLEXIS_OK;
+}
+
+int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int64_t *n_out) {
+    if (i < 0 || i >= g->last_P || g->last_sel <= 0 || !g->ws.sel_buf) return FLEXIS_E_INVALID;
+    CK(cudaSetDevice(g->device));
+    PatState s;
+    CK(cudaMemcpy(&s, g->ws.st + i, sizeof s, cudaMemcpyDeviceToHost));
+    int64_t n = std::min<int64_t>(s.logged, cap);
+    if (n > 0)
+        CK(cudaMemcpy(maps_out, g->ws.sel_buf + (size_t)i * g->last_sel * MAXN,
+                      sizeof(int32_t) * n * MAXN, cudaMemcpyDeviceToHost));
+    *n_out = n;
+    return FLEXIS_OK;
+}
+
+// ------------------------------------------------------------------ serving session
+// Continuous batching at round granularity: each step admits new plans into free slots, runs
+// one speculation round over every slot still in its greedy phase, runs the MNI search for the
+// slots that finished their greedy phase in that round, and returns every slot's phase and
+// result.  Requests admitted at different steps share the device rounds.
+struct ServeSession {
+    DeviceGraph *g = nullptr;
+    Workspace w;
+    cudaStream_t stream = nullptr;
+    int32_t slots = 0;
+    int Wmin = 32, Wmax = 512;
+    int32_t *d_admit = nullptr;
+    int32_t *h_admit = nullptr;  // pinned
+    Plan *h_plans = nullptr;     // pinned staging
+    PatState *h_st = nullptr;    // pinned
+    flexis_support_result *h_res = nullptr;  // pinned
+    int64_t round = 0;
+    int sblocks = 0;
+};
+
+int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out) {
+    CK(cudaSetDevice(g->device));
+    ServeSession *s = new ServeSession();
+    s->g = g;
+    s->slots = slots;
+    int rc = ws_ensure(g, s->w, slots, s->Wmax, 0);
+    if (rc) { serve_destroy(s); return rc; }
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&s->d_admit, sizeof(int32_t) * slots) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_admit, sizeof(int32_t) * slots) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_plans, sizeof(Plan) * slots) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_st, sizeof(PatState) * slots) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_res, sizeof(flexis_support_result) * slots) != cudaSuccess) {
+        serve_destroy(s);
+        return FLEXIS_E_NOMEM;
+    }
+    EvalConfig cfg;
+    s->sblocks = search_grid(g, cfg);
+    // every slot starts free
+    CK(cudaMemsetAsync(s->w.st, 0, sizeof(PatState) * slots, s->stream));
+    Batch B = make_batch(g, s->w, s->w.plans, slots, s->Wmin, s->Wmax, 0, s->w.results);
+    k_reset_ctl<<<1, 1, 0, s->stream>>>(B);
+    CK(cudaStreamSynchronize(s->stream));
+    *out = s;
+    return FLEXIS_OK;
+}
+
+void serve_destroy(ServeSession *s) {
+    if (!s) return;
+    cudaSetDevice(s->g->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    ws_free(s->w);
+    cudaFree(s->d_admit);
+    if (s->h_admit) cudaFreeHost(s->h_admit);
+    if (s->h_plans) cudaFreeHost(s->h_plans);
+    if (s->h_st) cudaFreeHost(s->h_st);
+    if (s->h_res) cudaFreeHost(s->h_res);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int serve_slot_bytes(const DeviceGraph *g, int64_t *bytes) {
+    *bytes = (int64_t)g->view.words * 4 + 512ll * (4 + 4 + 4 * MAXN + 8) + (int64_t)sizeof(PatState) +
+             (int64_t)sizeof(Plan);
+    return FLEXIS_OK;
+}
+
+int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_plans, int32_t n_admit,
+               int32_t *phase_out, flexis_support_result *res_out, int32_t *n_greedy) {
+    DeviceGraph *g = s->g;
+    CK(cudaSetDevice(g->device));
+    Batch B = make_batch(g, s->w, s->w.plans, s->slots, s->Wmin, s->Wmax, 0, s->w.results);
+    for (int32_t i = 0; i < n_admit; i++) {
+        s->h_admit[i] = admit_slots[i];
+        s->h_plans[i] = admit_plans[i];
+        CK(cudaMemcpyAsync(s->w.plans + admit_slots[i], &s->h_plans[i], sizeof(Plan),
+                           cudaMemcpyHostToDevice, s->stream));
+    }
+    if (n_admit > 0) {
+        CK(cudaMemcpyAsync(s->d_admit, s->h_admit, sizeof(int32_t) * n_admit, cudaMemcpyHostToDevice, s->stream));
+        k_admit<<<n_admit, 256, 0, s->stream>>>(B, s->d_admit, n_admit);
+    }
+    const int q = (int)(s->round & 1);
+    k_commit<<<s->slots, COMMIT_THREADS, commit_smem(s->Wmax), s->stream>>>(B, q);
+    k_search<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
+    s->round++;
+    k_mni_setup<<<1, 1024, 0, s->stream>>>(B);
+    k_mni<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B);
+    k_finalize<<<(s->slots + 255) / 256, 256, 0, s->stream>>>(B);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(s->h_st, s->w.st, sizeof(PatState) * s->slots, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_res, s->w.results, sizeof(flexis_support_result) * s->slots,
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    int32_t ng = 0;
+    for (int32_t i = 0; i < s->slots; i++) {
+        phase_out[i] = s->h_st[i].phase;
+        if (s->h_st[i].phase == PH_GREEDY) ng++;
+        if (s->h_st[i].phase == PH_READY) res_out[i] = s->h_res[i];
+    }
+    *n_greedy = ng;
+    return FLEXIS_OK;
+}
+
+}  // namespace fx

@@ -1,0 +1,439 @@
+// Host pattern compiler: canonical form (the role Bliss plays in the paper, Sec. 2.1.5),
+// automorphism orbits, matching orders, tau (Eq. tau), and candidate generation by core-group
+// merging (Algorithms 2-4, Sec. 3.2.1).
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "fx.h"
+
+namespace fx {
+
+bool Code::operator<(const Code &o) const {
+    if (n != o.n) return n < o.n;
+    for (int i = 0; i < n; i++)
+        if (lab[i] != o.lab[i]) return lab[i] < o.lab[i];
+    return bits < o.bits;
+}
+
+bool Code::operator==(const Code &o) const {
+    if (n != o.n || bits != o.bits) return false;
+    for (int i = 0; i < n; i++)
+        if (lab[i] != o.lab[i]) return false;
+    return true;
+}
+
+size_t CodeHash::operator()(const Code &c) const {
+    uint64_t h = 0x9E3779B97F4A7C15ull * (uint64_t)(c.n + 1) ^ c.bits;
+    for (int i = 0; i < c.n; i++) h = (h ^ (uint64_t)(uint32_t)c.lab[i]) * 0x100000001B3ull;
+    return (size_t)(h ^ (h >> 29));
+}
+
+static inline bool has(const Pat &p, int i, int j) { return (p.adj[i] >> j) & 1; }
+
+bool connected(const Pat &p) {
+    if (p.n == 0) return false;
+    int seen = 1, frontier = 1;
+    while (frontier) {
+        int nxt = 0;
+        for (int u = 0; u < p.n; u++)
+            if (frontier >> u & 1) nxt |= p.adj[u];
+        nxt &= ~seen;
+        seen |= nxt;
+        frontier = nxt;
+    }
+    return seen == (1 << p.n) - 1;
+}
+
+int edge_count(const Pat &p) {
+    int m = 0;
+    for (int i = 0; i < p.n; i++) m += __builtin_popcount(p.adj[i]);
+    return m / 2;
+}
+
+// ---------------------------------------------------------------- canonical form
+// Code of an order (position -> vertex): labels in order, then for columns j = 1..n-1 and rows
+// i = 0..j-1 the bit "not adjacent"; the canonical code is the lexicographic minimum over all
+// orders.  Search: positions are filled left to right; the label of each position is forced
+// (sorted label multiset), and a partial order whose bit prefix already exceeds the best
+// prefix is pruned.  The minimum over the pruned search equals the minimum over all n! orders.
+namespace {
+struct CanonSearch {
+    const Pat *p;
+    int n;
+    int32_t slab[MAXN];
+    int perm[MAXN];
+    int best_perm[MAXN];
+    uint32_t best_bits;
+    bool have;
+    int total_bits;
+
+    void rec(int pos, int used, uint32_t bits, int nb) {
+        if (pos == n) {
+            if (!have || bits < best_bits) {
+                best_bits = bits;
+                memcpy(best_perm, perm, sizeof(int) * n);
+                have = true;
+            }
+            return;
+        }
+        if (pos >= MAXN) return;
+        for (int w = 0; w < n; w++) {
+            if (used >> w & 1) continue;
+            if (p->lab[w] != slab[pos]) continue;
+            uint32_t b = bits;
+            for (int i = 0; i < pos; i++) b = (b << 1) | (has(*p, perm[i], w) ? 0u : 1u);
+            int nb2 = nb + pos;
+            // prune: this prefix already exceeds the best code's prefix
+            if (have && nb2 > 0 && b > (best_bits >> (total_bits - nb2))) continue;
+            perm[pos] = w;
+            rec(pos + 1, used | (1 << w), b, nb2);
+        }
+    }
+};
+}  // namespace
+
+Code canonical(const Pat &p, int *perm) {
+    CanonSearch s;
+    s.p = &p;
+    s.n = p.n;
+    for (int i = 0; i < p.n; i++) s.slab[i] = p.lab[i];
+    std::sort(s.slab, s.slab + p.n);
+    s.have = false;
+    s.best_bits = 0;
+    s.total_bits = p.n * (p.n - 1) / 2;
+    s.rec(0, 0, 0, 0);
+    Code c;
+    c.n = p.n;
+    for (int i = 0; i < p.n; i++) c.lab[i] = s.slab[i];
+    c.bits = s.best_bits;
+    if (perm) memcpy(perm, s.best_perm, sizeof(int) * p.n);
+    return c;
+}
+
+Pat pat_of_code(const Code &c) {
+    Pat p;
+    p.n = c.n;
+    for (int i = 0; i < c.n; i++) p.lab[i] = c.lab[i];
+    int t = c.n * (c.n - 1) / 2 - 1;
+    for (int j = 1; j < c.n; j++)
+        for (int i = 0; i < j; i++, t--)
+            if (!((c.bits >> t) & 1)) {
+                p.adj[i] |= (uint8_t)(1 << j);
+                p.adj[j] |= (uint8_t)(1 << i);
+            }
+    return p;
+}
+
+// ---------------------------------------------------------------- automorphisms and orbits
+namespace {
+struct AutSearch {
+    const Pat *p;
+    std::vector<std::array<int8_t, MAXN>> *out;
+    size_t limit;
+    int img[MAXN];
+    void rec(int pos, int used) {
+        if (out->size() >= limit) return;
+        if (pos == p->n) {
+            std::array<int8_t, MAXN> a{};
+            for (int i = 0; i < p->n; i++) a[i] = (int8_t)img[i];
+            out->push_back(a);
+            return;
+        }
+        for (int w = 0; w < p->n; w++) {
+            if (used >> w & 1) continue;
+            if (p->lab[w] != p->lab[pos]) continue;
+            if (__builtin_popcount(p->adj[w]) != __builtin_popcount(p->adj[pos])) continue;
+            bool ok = true;
+            for (int i = 0; i < pos && ok; i++)
+                if (has(*p, i, pos) != has(*p, img[i], w)) ok = false;
+            if (!ok) continue;
+            img[pos] = w;
+            rec(pos + 1, used | (1 << w));
+        }
+    }
+};
+}  // namespace
+
+void automorphisms(const Pat &p, std::vector<std::array<int8_t, MAXN>> *out, size_t limit) {
+    AutSearch s;
+    s.p = &p;
+    s.out = out;
+    s.limit = limit;
+    s.rec(0, 0);
+}
+
+void orbits(const Pat &p, int *orb) {
+    // u ~ v iff some automorphism maps u to v; orb[v] = smallest vertex of v's orbit
+    std::vector<std::array<int8_t, MAXN>> all;
+    automorphisms(p, &all, SIZE_MAX);
+    for (int v = 0; v < p.n; v++) {
+        orb[v] = v;
+        for (auto &a : all) orb[v] = std::min(orb[v], (int)a[v]);
+    }
+}
+
+LevelPlan level_plan(const Pat &q, int first) {
+    LevelPlan L;
+    memset(&L, 0, sizeof L);
+    int order[MAXN];
+    int visited = 1 << first;
+    order[0] = first;
+    for (int k = 1; k < q.n; k++) {
+        int pick = -1;
+        int reach = 0;
+        for (int u = 0; u < q.n; u++)
+            if (visited >> u & 1) reach |= q.adj[u];
+        reach &= ~visited;
+        pick = __builtin_ctz((unsigned)reach);  // smallest unvisited position adjacent to visited
+        order[k] = pick;
+        visited |= 1 << pick;
+    }
+    for (int i = 0; i < q.n; i++) {
+        L.vert[i] = (uint8_t)order[i];
+        L.lab[i] = (uint8_t)q.lab[order[i]];
+        uint8_t bm = 0, im = 0;
+        for (int j = 0; j < i; j++) {
+            if (has(q, order[j], order[i])) bm |= (uint8_t)(1 << j);
+            if (q.lab[order[j]] == q.lab[order[i]]) im |= (uint8_t)(1 << j);
+        }
+        L.bmask[i] = bm;
+        L.injmask[i] = im;
+    }
+    return L;
+}
+
+// ---------------------------------------------------------------- tau and plans
+int64_t tau_exact(int64_t sigma, int64_t lam_num, int64_t lam_den, int n) {
+    __int128 top = (__int128)sigma * ((__int128)(n - 1) * lam_num + lam_den);
+    __int128 bot = (__int128)n * lam_den;
+    return (int64_t)(top / bot);
+}
+
+int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, int64_t lam_num,
+                 int64_t lam_den, int mode, Plan &P) {
+    memset(&P, 0, sizeof P);
+    P.status = FLEXIS_E_INVALID;
+    P.n = pat.n;
+    P.sigma = sigma;
+    P.mode = mode;
+    if (pat.n < 2 || pat.n > MAXN || pat.m < 0 || pat.labels == nullptr ||
+        (pat.m > 0 && pat.edges == nullptr))
+        return FLEXIS_E_INVALID;
+    if (sigma < 1 || lam_den <= 0 || lam_num < 0 || lam_num > lam_den) return FLEXIS_E_INVALID;
+    if (mode != FLEXIS_MODE_EARLY && mode != FLEXIS_MODE_FULL) return FLEXIS_E_INVALID;
+    Pat p;
+    p.n = pat.n;
+    for (int i = 0; i < pat.n; i++) {
+        if (pat.labels[i] < 0) return FLEXIS_E_INVALID;
+        p.lab[i] = pat.labels[i];
+    }
+    for (int e = 0; e < pat.m; e++) {
+        int a = pat.edges[2 * e], b = pat.edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= pat.n || b >= pat.n || a == b) return FLEXIS_E_INVALID;
+        p.adj[a] |= (uint8_t)(1 << b);
+        p.adj[b] |= (uint8_t)(1 << a);
+    }
+    if (!connected(p)) return FLEXIS_E_INVALID;
+    P.n_edges = edge_count(p);
+    P.tau = tau_exact(sigma, lam_num, lam_den, pat.n);
+    int64_t c = P.tau > 1 ? P.tau : 1;
+    P.cap = mode == FLEXIS_MODE_EARLY ? c : CAP_INF;
+    P.status = FLEXIS_OK;
+    // labels -> ranks; an absent label means no map at all
+    for (int i = 0; i < pat.n; i++) {
+        int32_t r = pat.labels[i] < g.nl_ids ? g.rank_of[pat.labels[i]] : -1;
+        if (r < 0) {
+            P.flags |= FLEXIS_FLAG_ABSENT_LABEL;
+            P.root_begin = P.root_end = 0;
+            P.n_orb = 0;
+            return FLEXIS_OK;
+        }
+        p.lab[i] = r;
+    }
+    Code code = canonical(p, nullptr);
+    Pat q = pat_of_code(code);
+    P.code_n = code.n;
+    for (int i = 0; i < code.n; i++) P.code_lab[i] = code.lab[i];
+    P.code_bits = code.bits;
+    P.greedy = level_plan(q, 0);
+    P.root_begin = g.lab_ptr[q.lab[0]];
+    P.root_end = g.lab_ptr[q.lab[0] + 1];
+    int orb[MAXN];
+    orbits(q, orb);
+    int k = 0;
+    for (int u = 0; u < q.n; u++) {
+        if (orb[u] != u) continue;
+        P.orb[k] = level_plan(q, u);
+        P.orb_begin[k] = g.lab_ptr[q.lab[u]];
+        P.orb_end[k] = g.lab_ptr[q.lab[u] + 1];
+        k++;
+    }
+    P.n_orb = k;
+    return FLEXIS_OK;
+}
+
+// ---------------------------------------------------------------- candidate generation
+// Algorithm 2: core groups (Sec. 2.3.3) -> merge every pair of core graphs of a group under
+// every automorphism of the common core Gamma (Algorithm 3 returns either all automorphisms
+// or the identity; using all of them always is a superset that duplicate removal reduces to
+// the same set) -> cliques by a third core graph plus the post-check that every (k-1)-sub-clique
+// is frequent (Algorithm 4) -> RemoveDuplicates by canonical code.
+namespace {
+struct CoreEntry {
+    int32_t lab;    // marked vertex label
+    uint8_t mask;   // marked vertex attachment over the core's canonical positions
+    bool operator<(const CoreEntry &o) const { return lab != o.lab ? lab < o.lab : mask < o.mask; }
+    bool operator==(const CoreEntry &o) const { return lab == o.lab && mask == o.mask; }
+};
+
+struct Group {
+    Code core;
+    std::vector<std::array<int8_t, MAXN>> aut;
+    std::vector<CoreEntry> entries;
+};
+
+uint8_t map_mask(uint8_t m, const std::array<int8_t, MAXN> &a, int n) {
+    uint8_t r = 0;
+    for (int i = 0; i < n; i++)
+        if (m >> i & 1) r |= (uint8_t)(1 << a[i]);
+    return r;
+}
+}  // namespace
+
+void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<Code> &out,
+                         int threads) {
+    out.clear();
+    if (F.empty()) return;
+    std::unordered_set<Code, CodeHash> Fset(F.begin(), F.end());
+    // core groups
+    std::unordered_map<Code, size_t, CodeHash> gidx;
+    std::vector<Group> groups;
+    std::vector<int32_t> labels;
+    for (const Code &c : F) {
+        Pat P = pat_of_code(c);
+        for (int i = 0; i < P.n; i++) labels.push_back(P.lab[i]);
+        for (int x = 0; x < P.n; x++) {
+            Pat core;
+            core.n = P.n - 1;
+            int pos[MAXN], k = 0;
+            for (int i = 0; i < P.n; i++)
+                if (i != x) pos[k++] = i;
+            for (int i = 0; i < core.n; i++) {
+                core.lab[i] = P.lab[pos[i]];
+                for (int j = 0; j < core.n; j++)
+                    if (has(P, pos[i], pos[j])) core.adj[i] |= (uint8_t)(1 << j);
+            }
+            int perm[MAXN];
+            Code cc = canonical(core, perm);
+            // attachment of x over the core's canonical positions
+            uint8_t mask = 0;
+            for (int cp = 0; cp < core.n; cp++)
+                if (has(P, x, pos[perm[cp]])) mask |= (uint8_t)(1 << cp);
+            auto it = gidx.find(cc);
+            size_t gi;
+            if (it == gidx.end()) {
+                gi = groups.size();
+                gidx.emplace(cc, gi);
+                groups.push_back(Group{cc, {}, {}});
+            } else {
+                gi = it->second;
+            }
+            groups[gi].entries.push_back(CoreEntry{P.lab[x], mask});
+        }
+    }
+    std::sort(labels.begin(), labels.end());
+    labels.erase(std::unique(labels.begin(), labels.end()), labels.end());
+
+    std::vector<std::vector<Code>> part((size_t)std::max(1, threads));
+    std::atomic<size_t> next{0};
+    auto work = [&](int tid) {
+        std::unordered_set<Code, CodeHash> local;
+        for (;;) {
+            size_t gi = next.fetch_add(1);
+            if (gi >= groups.size()) break;
+            Group &G = groups[gi];
+            Pat core = pat_of_code(G.core);
+            std::vector<std::array<int8_t, MAXN>> aut;
+            automorphisms(core, &aut, SIZE_MAX);
+            // entries up to Aut(core): keep one representative (minimum mask image)
+            std::vector<CoreEntry> ent;
+            for (auto e : G.entries) {
+                uint8_t best = e.mask;
+                for (auto &a : aut) best = std::min(best, map_mask(e.mask, a, core.n));
+                ent.push_back(CoreEntry{e.lab, best});
+            }
+            std::sort(ent.begin(), ent.end());
+            ent.erase(std::unique(ent.begin(), ent.end()), ent.end());
+            int kc = core.n;
+            int core_edges = edge_count(core);
+            for (size_t a = 0; a < ent.size(); a++)
+                for (size_t b = a; b < ent.size(); b++)
+                    for (auto &al : aut) {
+                        uint8_t mb = map_mask(ent[b].mask, al, kc);
+                        int m = core_edges + __builtin_popcount(ent[a].mask) + __builtin_popcount(mb);
+                        if (max_edges > 0 && m > max_edges) continue;
+                        Pat P = core;
+                        P.n = kc + 2;
+                        int x = kc, y = kc + 1;
+                        P.lab[x] = ent[a].lab;
+                        P.lab[y] = ent[b].lab;
+                        P.adj[x] = ent[a].mask;
+                        P.adj[y] = mb;
+                        for (int i = 0; i < kc; i++) {
+                            if (ent[a].mask >> i & 1) P.adj[i] |= (uint8_t)(1 << x);
+                            if (mb >> i & 1) P.adj[i] |= (uint8_t)(1 << y);
+                        }
+                        if (!connected(P)) continue;
+                        local.insert(canonical(P, nullptr));
+                    }
+        }
+        part[(size_t)tid].assign(local.begin(), local.end());
+    };
+    int T = std::max(1, threads);
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto &t : th) t.join();
+    std::unordered_set<Code, CodeHash> all;
+    for (auto &v : part) all.insert(v.begin(), v.end());
+    // cliques (Algorithm 4 + post-check): a k-clique whose every (k-1)-sub-clique is frequent
+    for (const Code &c : F) {
+        Pat Q = pat_of_code(c);
+        int kq = Q.n;
+        if (edge_count(Q) != kq * (kq - 1) / 2) continue;
+        if (kq + 1 > MAXN) continue;
+        int m = kq * (kq + 1) / 2;
+        if (max_edges > 0 && m > max_edges) continue;
+        for (int32_t l : labels) {
+            Pat P = Q;
+            P.n = kq + 1;
+            P.lab[kq] = l;
+            P.adj[kq] = (uint8_t)((1 << kq) - 1);
+            for (int i = 0; i < kq; i++) P.adj[i] |= (uint8_t)(1 << kq);
+            bool ok = true;
+            for (int u = 0; u < P.n && ok; u++) {
+                Pat R;
+                R.n = P.n - 1;
+                int k = 0;
+                for (int i = 0; i < P.n; i++) {
+                    if (i == u) continue;
+                    R.lab[k] = P.lab[i];
+                    k++;
+                }
+                for (int i = 0; i < R.n; i++) R.adj[i] = (uint8_t)(((1 << R.n) - 1) & ~(1 << i));
+                if (!Fset.count(canonical(R, nullptr))) ok = false;
+            }
+            if (ok) all.insert(canonical(P, nullptr));
+        }
+    }
+    out.assign(all.begin(), all.end());
+    std::sort(out.begin(), out.end());
+}
+
+}  // namespace fx

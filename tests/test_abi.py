@@ -1,0 +1,118 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol include/flexis.h declares,
+and its host logic (canonical code, candidate generation, tau) agrees with the oracle.  No call
+here touches a GPU."""
+from __future__ import annotations
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2404_01585_gb300 as fx
+from workloads import Stream
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2404_01585_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "flexis.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(flexis_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 20
+    L = fx.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(fx.SYMBOLS)
+
+
+def test_struct_sizes_match_header():
+    import ctypes as C
+    assert C.sizeof(fx.flexis_options) == 64
+    assert C.sizeof(fx.flexis_support_result) == 64
+    assert C.sizeof(fx.flexis_plan) == 512
+
+
+def test_status_strings():
+    assert fx.status_string(0) == "ok"
+    assert fx.status_string(fx.FLEXIS_E_INVALID) == "invalid argument"
+
+
+def random_patterns(count, seed, max_n=7, labels=3):
+    st = Stream(seed)
+    out = []
+    for _ in range(count):
+        n = 2 + int(st.integers(1, max_n - 1)[0])
+        e = [(i, j) for i in range(n) for j in range(i + 1, n) if st.uniform(1)[0] < 0.45]
+        lab = [int(x) for x in st.integers(n, labels)]
+        out.append((lab, e))
+    return out
+
+
+def test_canonical_code_matches_oracle():
+    for lab, e in random_patterns(400, 3, max_n=8):
+        a = fx.canonical_code(lab, e)
+        b = oracle.canonical(lab, e)
+        assert a[:2] == b[:2]
+
+
+def test_candidate_generation_paper_figures():
+    R, B, G, Y = 0, 1, 2, 3
+    tri = [(0, 1), (1, 2), (0, 2)]
+    for F in ([([R, B, R], tri), ([B, B, R], tri)],
+              [([B, R, R, R], [(0, 1), (1, 2), (0, 2), (1, 3)])],
+              [([R, G, B], tri), ([R, G, Y], tri), ([R, B, Y], tri), ([G, B, Y], tri)],
+              [([R, G, B], tri), ([R, G, Y], tri), ([R, B, Y], tri)]):
+        assert fx.generate_candidates(F) == oracle.candidates(F)
+
+
+def _connected(n, e):
+    adj = {i: set() for i in range(n)}
+    for a, b in e:
+        adj[a].add(b)
+        adj[b].add(a)
+    seen = {0}
+    st = [0]
+    while st:
+        u = st.pop()
+        for v in adj[u] - seen:
+            seen.add(v)
+            st.append(v)
+    return len(seen) == n
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_candidate_generation_matches_oracle_predicate(k):
+    # merge-based generator (Algorithms 2-4) == predicate form, on random frequent sets
+    st = Stream(100 + k)
+    for trial in range(4):
+        F = []
+        seen = set()
+        for _attempt in range(400):
+            if len(F) >= 14:
+                break
+            n = k - 1
+            e = [(i, j) for i in range(n) for j in range(i + 1, n) if st.uniform(1)[0] < 0.5]
+            if not e or not _connected(n, e):
+                continue
+            lab = [int(x) for x in st.integers(n, 2)]
+            c = oracle.canonical(lab, e)[:2]
+            if c in seen:
+                continue
+            seen.add(c)
+            F.append((lab, e))
+        for me in (0, k + 1):
+            assert fx.generate_candidates(F, me) == oracle.candidates(F, me)

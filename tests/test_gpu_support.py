@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, element by element.
+
+All quantities are integers, so the bar is bit-exact: mis, mni, tau, the frequent flag, the
+selected maps themselves, and the frequent-pattern sets of mining."""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2404_01585_gb300 as fx
+from tests.test_oracle import tiny_cases
+from workloads import make_graph, random_patterns
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+EARLY, FULL = fx.FLEXIS_MODE_EARLY, fx.FLEXIS_MODE_FULL
+SHAPES = ["tree", "cycle", "clique", "path", "star"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def key(r):
+    return (r["tau"], r["mis"], r["mni"], bool(r["frequent"]))
+
+
+def check_batch(g, og, pats, sigma, lam, mode, tier=1):
+    res = g.support_batch(pats, sigma, lam, mode)
+    m = "early" if mode == EARLY else "full"
+    for (pl, pe), r in zip(pats, res):
+        assert r["status"] == 0
+        w = og.support(pl, pe, sigma=sigma, lam=lam, mode=m, tier=tier)
+        assert key(r) == (w["tau"], w["mis"], w["mni"], w["frequent"]), (pl, pe, r, w)
+    return res
+
+
+def load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def test_running_example_all_seeds():
+    d = load("running_example.json")
+    e = np.asarray(d["data_edges"])
+    for seed in range(32):
+        g = fx.Graph(d["data_labels"], e[:, 0], e[:, 1], seed=seed, record_selected=16)
+        og = oracle.Graph(d["data_labels"], e[:, 0], e[:, 1], seed=seed)
+        for P in (d["P1"], d["P2"]):
+            for mode, m in ((FULL, "full"), (EARLY, "early")):
+                for sigma, lam in ((2, 1.0), (2, 0.25), (3, 1.0)):
+                    r = g.support(P["labels"], P["edges"], sigma, lam, mode=mode)
+                    w = og.support(P["labels"], P["edges"], sigma=sigma, lam=lam, mode=m, tier=0,
+                                   want_selected=True)
+                    assert key(r) == (w["tau"], w["mis"], w["mni"], w["frequent"])
+                    assert g.selected_maps(0, 3) == w["selected"][: r["mis"]]
+        g.close()
+
+
+def test_theorem1_example_all_seeds():
+    d = load("malvisual.json")
+    e = np.asarray(d["data_edges"])
+    for seed in range(64):
+        g = fx.Graph(d["data_labels"], e[:, 0], e[:, 1], seed=seed, record_selected=16)
+        og = oracle.Graph(d["data_labels"], e[:, 0], e[:, 1], seed=seed)
+        r = g.support(d["P"]["labels"], d["P"]["edges"], 1, 1.0, mode=FULL)
+        w = og.support(d["P"]["labels"], d["P"]["edges"], sigma=1, lam=1.0, mode="full", tier=0,
+                       want_selected=True)
+        assert (r["mis"], r["mni"]) == (w["mis"], w["mni"]) and r["mni"] == 5
+        assert g.selected_maps(0, 4) == w["selected"]
+        g.close()
+
+
+def test_tiny_random_graphs_exhaustive_oracle():
+    for lab, src, dst, pl, pe, s in tiny_cases(120, 17):
+        g = fx.Graph(lab, src, dst, seed=s)
+        og = oracle.Graph(lab, src, dst, seed=s)
+        for mode in (FULL, EARLY):
+            for sigma, lam in ((1, 1.0), (3, 0.5), (5, 0.0)):
+                check_batch(g, og, [(pl, pe)], sigma, lam, mode, tier=0)
+        g.close()
+
+
+@pytest.fixture(scope="module")
+def powerlaw():
+    lab, src, dst = make_graph(kind="cl", nv=20000, ne=100000, nl=8, law="zipf", zipf_s=1.0,
+                               gamma=2.3, seed=41)
+    pats = random_patterns(80, range(2, 9), SHAPES, lab, 43)
+    return lab, src, dst, pats
+
+
+@pytest.mark.parametrize("mode", [EARLY, FULL])
+def test_powerlaw_batch_vs_oracle(powerlaw, mode):
+    lab, src, dst, pats = powerlaw
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    for sigma, lam in ((60, 0.5), (400, 1.0), (5, 0.0)):
+        check_batch(g, og, pats, sigma, lam, mode)
+    g.close()
+
+
+def test_plain_equals_batched_and_launch_shape_free(powerlaw):
+    lab, src, dst, pats = powerlaw
+    ref = None
+    for opts in ({}, dict(window_min=1, window_max=32), dict(window_min=1024, window_max=1024),
+                 dict(search_blocks=3), dict(window_min=7, window_max=64, search_blocks=151)):
+        g = fx.Graph(lab, src, dst, **opts)
+        for mode in (EARLY, FULL):
+            batch = [key(r) for r in g.support_batch(pats, 60, 0.5, mode)]
+            if ref is None:
+                ref = {}
+            if mode not in ref:
+                ref[mode] = batch
+            assert batch == ref[mode], opts
+        plain = [key(g.support(pl, pe, 60, 0.5, mode=EARLY)) for pl, pe in pats[:12]]
+        assert plain == ref[EARLY][:12]
+        g.close()
+
+
+def test_selected_maps_equal_oracle(powerlaw):
+    lab, src, dst, pats = powerlaw
+    g = fx.Graph(lab, src, dst, record_selected=4096)
+    og = oracle.Graph(lab, src, dst)
+    res = g.support_batch(pats[:30], 60, 0.5, FULL)
+    for i, ((pl, pe), r) in enumerate(zip(pats[:30], res)):
+        w = og.support(pl, pe, sigma=60, lam=0.5, mode="full", tier=1, want_selected=True)
+        assert r["mis"] == w["mis"]
+        assert g.selected_maps(i, len(pl), 4096) == w["selected"][:4096]
+    g.close()
+
+
+def test_edge_cases():
+    lab, src, dst = make_graph(kind="er", nv=500, ne=1500, nl=3, law="uniform", zipf_s=None,
+                               gamma=None, seed=5)
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    # label absent from the graph: no map at all
+    r = g.support([0, 7], [(0, 1)], 1, 1.0, mode=FULL)
+    assert (r["mis"], r["mni"], r["frequent"]) == (0, 0, False) and r["flags"] & fx.FLEXIS_FLAG_ABSENT_LABEL
+    # invalid: disconnected pattern, n = 1, n = 9, lambda out of range, sigma < 1
+    for bad in (([0, 1, 2], [(0, 1)]), ([0], []), ([0] * 9, [(i, i + 1) for i in range(8)])):
+        with pytest.raises(fx.FlexisError):
+            g.support(bad[0], bad[1], 5, 0.5)
+    with pytest.raises(fx.FlexisError):
+        g.support([0, 1], [(0, 1)], 5, 1.5)
+    with pytest.raises(fx.FlexisError):
+        g.support([0, 1], [(0, 1)], 0, 0.5)
+    # per-pattern errors inside a batch do not fail the batch
+    res = g.support_batch([([0, 1], [(0, 1)]), ([0, 1, 2], [(0, 1)])], 5, 0.5)
+    assert res[0]["status"] == 0 and res[1]["status"] == fx.FLEXIS_E_INVALID
+    # n = 2 and n = 8, sigma far above anything, tau = 0 (cap 1)
+    pats = [([0, 1], [(0, 1)]), ([0] * 8, [(i, j) for i in range(8) for j in range(i + 1, 8)]),
+            ([0, 1, 2, 0, 1, 2, 0, 1], [(i, i + 1) for i in range(7)])]
+    for sigma, lam in ((1, 0.0), (2, 0.0), (10**9, 1.0), (7, 0.3)):
+        for mode in (EARLY, FULL):
+            check_batch(g, og, pats, sigma, lam, mode)
+    g.close()
+    # graph with isolated vertices and no edges
+    g = fx.Graph([0, 1, 0, 1], [], [])
+    r = g.support([0, 1], [(0, 1)], 1, 1.0, mode=FULL)
+    assert (r["mis"], r["mni"]) == (0, 0)
+    g.close()
+
+
+def test_mine_citeseer_shape():
+    lab, src, dst = make_graph("citeseer")
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    for sigma, lam, me in ((300, 0.5, 4), (30, 0.5, 4), (60, 0.0, 3)):
+        got, glev = g.mine(sigma, lam, me)
+        want, wlev = og.mine(sigma=sigma, lam=lam, max_edges=me)
+        assert glev == wlev
+        assert [(p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in got] == want
+    g.close()
+
+
+def test_mine_small_powerlaw(powerlaw):
+    lab, src, dst, _ = powerlaw
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    got, glev = g.mine(300, 0.5, 3)
+    want, wlev = og.mine(sigma=300, lam=0.5, max_edges=3)
+    assert glev == wlev
+    assert [(p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in got] == want
+    g.close()
+
+
+def test_serving_alone_equals_mixed(powerlaw):
+    lab, src, dst, pats = powerlaw
+    g = fx.Graph(lab, src, dst)
+    alone = [key(r) for r in g.support_batch(pats, 60, 0.5, EARLY)]
+    srv = fx.Server(g, slots=16)
+    import time
+    got = {}
+    for i, (pl, pe) in enumerate(pats):
+        assert srv.submit(i, pl, pe, 60, 0.5) == 0
+        if i % 7 == 0:
+            time.sleep(0.002)
+        for rid, r, lat in srv.poll():
+            got[rid] = r
+    t0 = time.time()
+    while len(got) < len(pats) and time.time() - t0 < 120:
+        for rid, r, lat in srv.poll():
+            got[rid] = r
+        time.sleep(0.001)
+    srv.stop()
+    assert [key(got[i]) for i in range(len(pats))] == alone
+    g.close()
