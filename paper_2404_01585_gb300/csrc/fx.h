@@ -24,6 +24,7 @@ struct LevelPlan {
     uint8_t bmask[MAXN];
     uint8_t injmask[MAXN];
     uint8_t vert[MAXN];
+    uint8_t deg[MAXN];     // pattern degree of the vertex bound at level i
 };
 
 // Compiled pattern (host pattern compiler output; plain bytes, device readable).
@@ -39,19 +40,19 @@ struct Plan {
     LevelPlan greedy;               // matching order rooted at canonical vertex 0
     LevelPlan orb[MAXN];            // matching order rooted at each orbit representative
     int32_t orb_begin[MAXN], orb_end[MAXN];  // candidate slice of the label index per orbit
-    int32_t code_lab[MAXN];         // canonical code: rank labels in canonical order
+    uint8_t code_lab[MAXN];         // canonical code: rank labels in canonical order
     uint32_t code_bits;             // canonical code: adjacency bits
     int32_t code_n;
 };
 static_assert(sizeof(Plan) <= sizeof(flexis_plan), "plan must fit flexis_plan");
 
-// Per-vertex record, one 16-byte load: adjacency offset, label-run offset, number of runs,
-// rank label.
+// Per-vertex record, one 16-byte load: adjacency offset, label-run offset, degree, and
+// (number of label runs << 8 | rank label).
 struct VRec {
     uint32_t adj;
     uint32_t run;
-    uint32_t nrun;
-    uint32_t lab;
+    uint32_t deg;
+    uint32_t meta;
 };
 
 // Host copy of the data graph layout (built on the host, mirrored on the device).

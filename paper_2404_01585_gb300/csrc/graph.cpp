@@ -148,7 +148,8 @@ int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_
                     g.runs[(size_t)(ro + j++)] = ((uint32_t)rk[(size_t)w] << 24) | (uint32_t)t;
             }
             g.runs[(size_t)(ro + j)] = (RUN_SENTINEL_LABEL << 24) | (uint32_t)k;
-            g.vrec[(size_t)v] = VRec{(uint32_t)o, (uint32_t)ro, (uint32_t)j, (uint32_t)rk[(size_t)v]};
+            g.vrec[(size_t)v] = VRec{(uint32_t)o, (uint32_t)ro, (uint32_t)k,
+                                     ((uint32_t)j << 8) | (uint32_t)rk[(size_t)v]};
         }
     });
     // label-partitioned vertex index in greedy-root order

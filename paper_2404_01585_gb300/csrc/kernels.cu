@@ -107,11 +107,12 @@ struct WarpState {
     int32_t t[MAXN];                    // data vertex bound at each level
     uint32_t lo[MAXN], hi[MAXN];        // driver slice of each level
     uint32_t pos[MAXN], base[MAXN], mask[MAXN];
+    uint32_t conf[MAXN];                // backjump conflict set of each level (bits of levels)
     uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
     int32_t nchk[MAXN];
     LevelPlan L;
     int32_t n;
-    int32_t pad[3];
+    int32_t pad[1];
 };
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
@@ -125,7 +126,7 @@ __device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uin
     const int lane = threadIdx.x & 31;
     const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec) + v);
     bytes += 16;
-    const uint32_t adj = r.x, run = r.y, nrun = r.z;
+    const uint32_t adj = r.x, run = r.y, nrun = r.w >> 8;
     lo = hi = 0;
     for (uint32_t j0 = 0; j0 < nrun; j0 += 32) {
         const uint32_t j = j0 + lane;
@@ -193,18 +194,25 @@ __device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W,
     return true;
 }
 
+// Candidate test at level i.  rej collects the earlier levels whose bound vertex caused a
+// rejection by injectivity (the conflict set of conflict-directed backjumping).
 __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
                                                 int32_t c, const uint32_t *used,
-                                                uint32_t &probes) {
+                                                uint32_t &probes, uint32_t &rej) {
     uint32_t im = W.L.injmask[i];
     while (im) {
         const int b = __ffs(im) - 1;
         im &= im - 1;
-        if (W.t[b] == c) return false;
+        if (W.t[b] == c) { rej |= 1u << b; return false; }
     }
     if (used) {
         probes++;
         if (used_bit(used, c)) return false;
+    }
+    // degree filter: a data vertex with fewer neighbours than the pattern vertex cannot host it
+    if (W.L.deg[i] > 1) {
+        probes += 4;
+        if (__ldg(&G.vrec[c].deg) < W.L.deg[i]) return false;
     }
     const int nchk = W.nchk[i];
     for (int k = 0; k < nchk; k++)
@@ -214,6 +222,14 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 
 // Lexicographically first map (in the level order of W.L) with level 0 bound to `root` and no
 // vertex in `used` (nullable).  On success W.t holds the map by level.
+//
+// Depth-first search with conflict-directed backjumping (Prosser, Computational Intelligence
+// 9(3), 1993): when every candidate of level i has failed, the search returns directly to the
+// deepest earlier level whose binding could change that outcome -- the levels that define
+// level i's candidate slices (its pattern neighbours), the levels whose vertex rejected a
+// candidate by injectivity, and the conflict levels handed up by deeper failures.  Levels in
+// between cannot make level i succeed, so skipping their remaining candidates removes only
+// subtrees without a map: the first map found in lexicographic order is unchanged.
 __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                           unsigned long long &bytes, uint32_t &probes) {
     const int lane = threadIdx.x & 31;
@@ -226,11 +242,16 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
     }
     int i = 1;
     bool ok = enter_level(G, W, 1, bytes);
-    uint32_t hi = 0, pos = 0, base = 0, mask = 0;
+    uint32_t hi = 0, pos = 0, base = 0, mask = 0, conf = 0;
     if (ok) { hi = W.hi[1]; pos = W.lo[1]; }
     for (;;) {
         if (!ok) {
-            if (--i == 0) return false;
+            // level i has no candidate left: jump to the deepest level of its conflict set
+            const uint32_t cs = (conf | W.L.bmask[i]) & ((1u << i) - 1u);
+            const int h = 31 - __clz(cs);
+            if (h <= 0) return false;  // only the root is to blame: this root has no map
+            conf = W.conf[h] | (cs & ~(1u << h));
+            i = h;
             hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i];
             ok = true;
             continue;
@@ -239,8 +260,10 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
             if (pos >= hi) { ok = false; continue; }
             const uint32_t k = pos + lane;
             bool good = false;
-            if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes);
+            uint32_t rej = 0;
+            if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes, rej);
             mask = __ballot_sync(FULLMASK, good);
+            conf |= __reduce_or_sync(FULLMASK, rej);
             bytes += 4ull * min(32u, hi - pos);
             base = pos;
             pos += 32;
@@ -251,9 +274,10 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
         const int32_t c = __ldg(G.adj + base + j);
         if (lane == 0) W.t[i] = c;
         if (i == n - 1) { __syncwarp(); return true; }
-        if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; }
+        if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
         __syncwarp();
         ++i;
+        conf = 0;
         ok = enter_level(G, W, i, bytes);
         if (ok) { hi = W.hi[i]; pos = W.lo[i]; mask = 0; }
     }
@@ -261,7 +285,8 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, int n) {
     const int lane = threadIdx.x & 31;
-    if (lane < 8) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
+    constexpr int WORDS = sizeof(LevelPlan) / 4;
+    if (lane < WORDS) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
     if (lane == 0) W.n = n;
     __syncwarp();
 }

@@ -204,6 +204,7 @@ LevelPlan level_plan(const Pat &q, int first) {
         }
         L.bmask[i] = bm;
         L.injmask[i] = im;
+        L.deg[i] = (uint8_t)__builtin_popcount(q.adj[order[i]]);
     }
     return L;
 }
@@ -259,7 +260,7 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
     Code code = canonical(p, nullptr);
     Pat q = pat_of_code(code);
     P.code_n = code.n;
-    for (int i = 0; i < code.n; i++) P.code_lab[i] = code.lab[i];
+    for (int i = 0; i < code.n; i++) P.code_lab[i] = (uint8_t)code.lab[i];
     P.code_bits = code.bits;
     P.greedy = level_plan(q, 0);
     P.root_begin = g.lab_ptr[q.lab[0]];

@@ -89,10 +89,31 @@ def test_tiny_random_graphs_exhaustive_oracle():
 
 @pytest.fixture(scope="module")
 def powerlaw():
+    # sizes the plain oracle finishes in seconds: its depth-first search has no backjumping, and
+    # 7-8 vertex trees and cycles through the hubs of this graph take it minutes
     lab, src, dst = make_graph(kind="cl", nv=20000, ne=100000, nl=8, law="zipf", zipf_s=1.0,
                                gamma=2.3, seed=41)
-    pats = random_patterns(80, range(2, 9), SHAPES, lab, 43)
+    pats = random_patterns(80, range(2, 7), SHAPES, lab, 43)
     return lab, src, dst, pats
+
+
+@pytest.fixture(scope="module")
+def er_large_patterns():
+    # 7 and 8 vertex patterns on a graph without hubs (the oracle stays fast)
+    lab, src, dst = make_graph(kind="er", nv=6000, ne=30000, nl=4, law="uniform", zipf_s=None,
+                               gamma=None, seed=47)
+    pats = random_patterns(40, range(7, 9), SHAPES, lab, 49)
+    return lab, src, dst, pats
+
+
+@pytest.mark.parametrize("mode", [EARLY, FULL])
+def test_large_patterns_vs_oracle(er_large_patterns, mode):
+    lab, src, dst, pats = er_large_patterns
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    for sigma, lam in ((30, 0.5), (2, 0.0)):
+        check_batch(g, og, pats, sigma, lam, mode)
+    g.close()
 
 
 @pytest.mark.parametrize("mode", [EARLY, FULL])
