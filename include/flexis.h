@@ -60,10 +60,14 @@ extern "C" {
 #define FLEXIS_MODE_FULL 0  /* exact mIS and exact MNI */
 #define FLEXIS_MODE_EARLY 1 /* stop at c = max(tau,1) (Sec. 3.1.1): mis = min(mIS, c),
                                mni = min(MNI, c); the frequent decision is unchanged */
+#define FLEXIS_MODE_NO_MNI 4 /* or-ed into a mode: skip the MNI count (mni = -1).  The paper's
+                                metric step (Sec. 3.2.2) computes the mIS only; mining uses
+                                FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI */
 
 /* result flags */
 #define FLEXIS_FLAG_ABSENT_LABEL 1u /* a pattern label does not occur in the data graph */
 #define FLEXIS_FLAG_MNI_FROM_MIS 2u /* mni follows from mis (mis reached c, or M is empty) */
+#define FLEXIS_FLAG_MNI_SKIPPED 4u  /* FLEXIS_MODE_NO_MNI: mni not computed (-1) */
 
 #define FLEXIS_MAX_PATTERN 8 /* largest pattern, in vertices */
 
@@ -102,14 +106,18 @@ typedef struct {
     int64_t mni;      /* minimum image count (capped in EARLY mode) */
     int32_t frequent; /* mis >= max(tau, 1) */
     uint32_t flags;   /* FLEXIS_FLAG_* */
-    int64_t roots_searched; /* diagnostic: root searches run (not part of the result) */
+    int64_t roots_searched; /* diagnostics below: not part of the result                      */
+                            /* root searches run by the greedy phase                          */
+    int64_t search_steps;   /* candidate chunks scanned by those searches                     */
+    int32_t max_item_steps; /* largest chunk count of one root search                         */
+    int32_t rounds;         /* speculation rounds the pattern took part in                    */
 } flexis_support_result;
 
 /* Precompiled pattern (host-side pattern compilation: canonical form, automorphism orbits,
  * matching orders, tau).  Plain bytes: may be copied to device memory and passed to
  * flexis_support_plans_device.                                                                 */
 typedef struct {
-    uint8_t bytes[512];
+    uint8_t bytes[1024];
 } flexis_plan;
 
 typedef struct {

@@ -28,8 +28,10 @@ FLEXIS_E_UNSUPPORTED = -6
 FLEXIS_E_BUSY = -7
 FLEXIS_MODE_FULL = 0
 FLEXIS_MODE_EARLY = 1
+FLEXIS_MODE_NO_MNI = 4
 FLEXIS_FLAG_ABSENT_LABEL = 1
 FLEXIS_FLAG_MNI_FROM_MIS = 2
+FLEXIS_FLAG_MNI_SKIPPED = 4
 LAMBDA_DEN = 1_000_000
 DEFAULT_SEED = 0x5EED
 
@@ -54,16 +56,18 @@ class flexis_pattern(C.Structure):
 class flexis_support_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("sigma", C.c_int64), ("tau", C.c_int64),
                 ("cap", C.c_int64), ("mis", C.c_int64), ("mni", C.c_int64),
-                ("frequent", C.c_int32), ("flags", C.c_uint32), ("roots_searched", C.c_int64)]
+                ("frequent", C.c_int32), ("flags", C.c_uint32), ("roots_searched", C.c_int64),
+                ("search_steps", C.c_int64), ("max_item_steps", C.c_int32), ("rounds", C.c_int32)]
 
     def as_dict(self):
         return dict(status=self.status, n=self.n, sigma=self.sigma, tau=self.tau, cap=self.cap,
                     mis=self.mis, mni=self.mni, frequent=bool(self.frequent), flags=self.flags,
-                    roots_searched=self.roots_searched)
+                    roots_searched=self.roots_searched, search_steps=self.search_steps,
+                    max_item_steps=self.max_item_steps, rounds=self.rounds)
 
 
 class flexis_plan(C.Structure):
-    _fields_ = [("bytes", C.c_uint8 * 512)]
+    _fields_ = [("bytes", C.c_uint8 * 1024)]
 
 
 class flexis_graph_info(C.Structure):
@@ -250,12 +254,12 @@ class Graph:
         return [out[i].as_dict() for i in range(cnt)]
 
     def compile(self, patterns, sigma, lam, mode=FLEXIS_MODE_EARLY) -> np.ndarray:
-        """Plans (uint8 [count, 512]) of the patterns, ready to be copied to device memory."""
+        """Plans (uint8 [count, 1024]) of the patterns, ready to be copied to device memory."""
         cnt = len(patterns)
         arr, keep = self._patterns(patterns)
         sig = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.int64), (cnt,)))
         num = np.ascontiguousarray(np.rint(np.broadcast_to(np.asarray(lam, np.float64), (cnt,)) * LAMBDA_DEN).astype(np.int64))
-        plans = np.zeros((max(1, cnt), 512), np.uint8)
+        plans = np.zeros((max(1, cnt), 1024), np.uint8)
         rc = lib().flexis_compile(self._h, arr, sig.ctypes.data_as(_I64P), num.ctypes.data_as(_I64P),
                                   LAMBDA_DEN, cnt, mode, plans.ctypes.data_as(C.POINTER(flexis_plan)))
         _check(rc, "flexis_compile")

@@ -247,7 +247,8 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
         for (size_t i = 0; i < C.size(); i++) {
             pattern_of_code(g, C[i], labels, edges);
             flexis_pattern p{(int32_t)labels.size(), (int32_t)(edges.size() / 2), labels.data(), edges.data()};
-            compile_plan(g->hg, p, sigma, num, LAMBDA_DEN, FLEXIS_MODE_EARLY, plans[i]);
+            // the metric step of Algorithm 1 needs the mIS decision only (Sec. 3.2.2)
+            compile_plan(g->hg, p, sigma, num, LAMBDA_DEN, FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI, plans[i]);
         }
         std::vector<flexis_support_result> res(C.size());
         int rc = eval_plans(g, plans, res.data());
@@ -255,6 +256,9 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
         std::vector<Code> F;
         for (size_t i = 0; i < C.size(); i++)
             if (res[i].status == FLEXIS_OK && res[i].frequent) {
+                // a frequent pattern has mIS >= c, hence MNI >= c: its capped MNI is c
+                res[i].mni = res[i].cap;
+                res[i].flags = (res[i].flags & ~FLEXIS_FLAG_MNI_SKIPPED) | FLEXIS_FLAG_MNI_FROM_MIS;
                 F.push_back(C[i]);
                 S->items.push_back({C[i], res[i]});
             }

@@ -39,20 +39,27 @@ struct Plan {
     int32_t n_edges;
     LevelPlan greedy;               // matching order rooted at canonical vertex 0
     LevelPlan orb[MAXN];            // matching order rooted at each orbit representative
-    int32_t orb_begin[MAXN], orb_end[MAXN];  // candidate slice of the label index per orbit
     uint8_t code_lab[MAXN];         // canonical code: rank labels in canonical order
+    uint8_t cadj[MAXN];             // canonical pattern adjacency rows (bit j: i ~ j)
     uint32_t code_bits;             // canonical code: adjacency bits
     int32_t code_n;
+    int32_t want_mni;               // 0 under FLEXIS_MODE_NO_MNI
+    int32_t lab_begin[MAXN], lab_end[MAXN];  // label-index slice of each canonical vertex's label
+    uint64_t need[MAXN];            // rank labels (< 64) of each canonical vertex's neighbours
 };
 static_assert(sizeof(Plan) <= sizeof(flexis_plan), "plan must fit flexis_plan");
 
-// Per-vertex record, one 16-byte load: adjacency offset, label-run offset, degree, and
-// (number of label runs << 8 | rank label).
-struct VRec {
+// Per-vertex record, one 32-byte sector: adjacency offset, label-run offset, degree,
+// (number of label runs << 8 | rank label), and the set of rank labels < 64 found among the
+// neighbours (a one-hop filter: a pattern vertex whose neighbours need label l cannot be hosted
+// by a data vertex without a neighbour of label l).
+struct alignas(32) VRec {
     uint32_t adj;
     uint32_t run;
     uint32_t deg;
     uint32_t meta;
+    uint64_t nbr_labels;
+    uint64_t pad;
 };
 
 // Host copy of the data graph layout (built on the host, mirrored on the device).

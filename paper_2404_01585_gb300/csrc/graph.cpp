@@ -141,15 +141,17 @@ int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_
             int64_t a = off[(size_t)v], k = kept[(size_t)v];
             int64_t o = koff[(size_t)v], ro = roff[(size_t)v];
             int64_t j = 0;
+            uint64_t lm = 0;
             for (int64_t t = 0; t < k; t++) {
                 int32_t w = tmp[(size_t)(a + t)];
                 g.adj[(size_t)(o + t)] = w;
+                if (rk[(size_t)w] < 64) lm |= 1ull << rk[(size_t)w];
                 if (t == 0 || rk[(size_t)w] != rk[(size_t)tmp[(size_t)(a + t - 1)]])
                     g.runs[(size_t)(ro + j++)] = ((uint32_t)rk[(size_t)w] << 24) | (uint32_t)t;
             }
             g.runs[(size_t)(ro + j)] = (RUN_SENTINEL_LABEL << 24) | (uint32_t)k;
             g.vrec[(size_t)v] = VRec{(uint32_t)o, (uint32_t)ro, (uint32_t)k,
-                                     ((uint32_t)j << 8) | (uint32_t)rk[(size_t)v]};
+                                     ((uint32_t)j << 8) | (uint32_t)rk[(size_t)v], lm, 0};
         }
     });
     // label-partitioned vertex index in greedy-root order

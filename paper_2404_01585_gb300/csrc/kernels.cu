@@ -67,6 +67,9 @@ struct PatState {
     int32_t phase;
     int32_t logged;    // selected maps written to the selection log
     unsigned long long mni_cnt[MAXN];
+    unsigned long long steps;  // candidate chunks scanned by the greedy searches
+    uint32_t max_steps;        // largest chunk count of one greedy search
+    uint32_t pad2;
 };
 
 struct Ctl {
@@ -110,6 +113,7 @@ struct WarpState {
     uint32_t conf[MAXN];                // backjump conflict set of each level (bits of levels)
     uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
     int32_t nchk[MAXN];
+    unsigned long long need[MAXN];      // neighbour labels each canonical vertex needs
     LevelPlan L;
     int32_t n;
     int32_t pad[1];
@@ -124,7 +128,7 @@ __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
 __device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uint32_t lab,
                                            uint32_t &lo, uint32_t &hi, unsigned long long &bytes) {
     const int lane = threadIdx.x & 31;
-    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec) + v);
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec + v));
     bytes += 16;
     const uint32_t adj = r.x, run = r.y, nrun = r.w >> 8;
     lo = hi = 0;
@@ -194,6 +198,18 @@ __device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W,
     return true;
 }
 
+// Static one-hop filter: a data vertex can host a pattern vertex only if its degree is at least
+// the pattern vertex's and every label the pattern vertex's neighbours carry (ranks < 64) occurs
+// among its own neighbours.  Depends on the data vertex alone, so it rejects only vertices that
+// belong to no map at all.
+__device__ __forceinline__ bool vertex_fits(const DevGraphView &G, int32_t c, uint32_t deg_req,
+                                            unsigned long long need) {
+    const VRec *r = G.vrec + c;
+    const uint32_t deg = __ldg(&r->deg);
+    const unsigned long long have = __ldg(reinterpret_cast<const unsigned long long *>(&r->nbr_labels));
+    return deg >= deg_req && (have & need) == need;
+}
+
 // Candidate test at level i.  rej collects the earlier levels whose bound vertex caused a
 // rejection by injectivity (the conflict set of conflict-directed backjumping).
 __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
@@ -209,11 +225,8 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
         probes++;
         if (used_bit(used, c)) return false;
     }
-    // degree filter: a data vertex with fewer neighbours than the pattern vertex cannot host it
-    if (W.L.deg[i] > 1) {
-        probes += 4;
-        if (__ldg(&G.vrec[c].deg) < W.L.deg[i]) return false;
-    }
+    probes += 4;
+    if (!vertex_fits(G, c, W.L.deg[i], W.need[W.L.vert[i]])) return false;
     const int nchk = W.nchk[i];
     for (int k = 0; k < nchk; k++)
         if (!contains(G.adj, W.clo[i][k], W.chi[i][k], c, probes)) return false;
@@ -231,7 +244,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // between cannot make level i succeed, so skipping their remaining candidates removes only
 // subtrees without a map: the first map found in lexicographic order is unchanged.
 __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
-                          unsigned long long &bytes, uint32_t &probes) {
+                          unsigned long long &bytes, uint32_t &probes, uint32_t &steps) {
     const int lane = threadIdx.x & 31;
     const int n = W.n;
     if (lane == 0) W.t[0] = root;
@@ -240,6 +253,8 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
         bytes += 4;
         if (used_bit(used, root)) return false;
     }
+    bytes += 32;
+    if (!vertex_fits(G, root, W.L.deg[0], W.need[W.L.vert[0]])) return false;
     int i = 1;
     bool ok = enter_level(G, W, 1, bytes);
     uint32_t hi = 0, pos = 0, base = 0, mask = 0, conf = 0;
@@ -265,6 +280,7 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
             bytes += 4ull * min(32u, hi - pos);
+            steps++;
             base = pos;
             pos += 32;
             continue;
@@ -283,11 +299,12 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
     }
 }
 
-__device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, int n) {
+__device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {
     const int lane = threadIdx.x & 31;
     constexpr int WORDS = sizeof(LevelPlan) / 4;
     if (lane < WORDS) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
-    if (lane == 0) W.n = n;
+    if (lane < MAXN) W.need[lane] = P.need[lane];
+    if (lane == 0) W.n = P.n;
     __syncwarp();
 }
 
@@ -358,10 +375,15 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch B, int q) {
         const int2 item = B.items[it];
         const int p = item.x, s = item.y;
         const Plan &P = B.plans[p];
-        load_level_plan(W, P.greedy, P.n);
+        load_level_plan(W, P.greedy, P);
         const size_t slot = (size_t)p * B.Wmax + s;
         const int32_t root = B.win_root[slot];
-        const bool found = dfs_first(B.G, W, B.used + (size_t)p * B.G.words, root, bytes, probes);
+        uint32_t steps = 0;
+        const bool found = dfs_first(B.G, W, B.used + (size_t)p * B.G.words, root, bytes, probes, steps);
+        if (lane == 0 && steps) {
+            atomicAdd(&B.st[p].steps, (unsigned long long)steps);
+            atomicMax(&B.st[p].max_steps, steps);
+        }
         if (lane == 0) B.win_state[slot] = found ? SLOT_MAP : SLOT_NONE;
         if (found && lane < P.n) B.win_map[slot * MAXN + lane] = W.t[lane];
         __syncwarp();
@@ -543,7 +565,8 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         int32_t r = -1;
         if (tid < chunk) {
             r = __ldg(B.G.lab_vtx + cursor + tid);
-            ok = used_bit(used, r) ? 0 : 1;
+            // a used root, or one that cannot host canonical vertex 0, has no map: decided now
+            ok = (!used_bit(used, r) && vertex_fits(B.G, r, P.greedy.deg[0], P.need[0])) ? 1 : 0;
         }
         if (tid == 0) { s_newcur = cursor + chunk; }
         __syncthreads();
@@ -617,9 +640,12 @@ __global__ void k_mni_setup(Batch B) {
             const int p = sidx / MAXN, o = sidx % MAXN;
             const Plan &P = B.plans[p];
             const PatState &S = B.st[p];
-            const bool need = S.phase == PH_MNI && P.status == FLEXIS_OK &&
+            const bool need = S.phase == PH_MNI && P.status == FLEXIS_OK && P.want_mni &&
                               !(P.flags & FLEXIS_FLAG_ABSENT_LABEL) && S.count < P.cap && S.count > 0;
-            if (need && o < P.n_orb) len = P.orb_end[o] - P.orb_begin[o];
+            if (need && o < P.n_orb) {
+                const int u = P.orb[o].vert[0];
+                len = P.lab_end[u] - P.lab_begin[u];
+            }
         }
         int excl;
         const int tot = block_scan(len, excl, sh);
@@ -666,12 +692,14 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
             unsigned long long *cnt = &B.st[p].mni_cnt[o];
             if ((long long)__ldcg(cnt) >= P.cap) continue;
             if (seg != cur_seg) {
-                load_level_plan(W, P.orb[o], P.n);
+                load_level_plan(W, P.orb[o], P);
                 cur_seg = seg;
             }
-            const int32_t d = __ldg(B.G.lab_vtx + P.orb_begin[o] + (int)(c - B.mni_seg[seg]));
+            const int u = P.orb[o].vert[0];
+            const int32_t d = __ldg(B.G.lab_vtx + P.lab_begin[u] + (int)(c - B.mni_seg[seg]));
             items++;
-            const bool found = dfs_first(B.G, W, nullptr, d, bytes, probes);
+            uint32_t steps = 0;
+            const bool found = dfs_first(B.G, W, nullptr, d, bytes, probes, steps);
             if (found && lane == 0) atomicAdd(cnt, 1ull);
         }
     }
@@ -698,11 +726,16 @@ __global__ void k_finalize(Batch B) {
     r.cap = P.mode == FLEXIS_MODE_EARLY ? P.cap : -1;
     r.flags = P.flags;
     r.roots_searched = S.searched;
+    r.search_steps = (int64_t)S.steps;
+    r.max_item_steps = (int32_t)S.max_steps;
+    r.rounds = S.rounds;
     if (P.status == FLEXIS_OK) {
         const int64_t cap = P.cap;
         const int64_t mis = S.count < cap ? S.count : cap;
         int64_t mni;
-        if (P.flags & FLEXIS_FLAG_ABSENT_LABEL) {
+        if (!P.want_mni) {
+            mni = -1;
+        } else if (P.flags & FLEXIS_FLAG_ABSENT_LABEL) {
             mni = 0;
         } else if (S.count >= cap || S.count == 0) {
             mni = S.count >= cap ? cap : 0;

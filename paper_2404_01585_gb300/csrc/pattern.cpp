@@ -222,7 +222,10 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
     P.status = FLEXIS_E_INVALID;
     P.n = pat.n;
     P.sigma = sigma;
+    P.want_mni = (mode & FLEXIS_MODE_NO_MNI) ? 0 : 1;
+    mode &= ~FLEXIS_MODE_NO_MNI;
     P.mode = mode;
+    if (!P.want_mni) P.flags |= FLEXIS_FLAG_MNI_SKIPPED;
     if (pat.n < 2 || pat.n > MAXN || pat.m < 0 || pat.labels == nullptr ||
         (pat.m > 0 && pat.edges == nullptr))
         return FLEXIS_E_INVALID;
@@ -262,17 +265,22 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
     P.code_n = code.n;
     for (int i = 0; i < code.n; i++) P.code_lab[i] = (uint8_t)code.lab[i];
     P.code_bits = code.bits;
+    for (int u = 0; u < q.n; u++) {
+        P.cadj[u] = q.adj[u];
+        for (int w = 0; w < q.n; w++)
+            if ((q.adj[u] >> w & 1) && q.lab[w] < 64) P.need[u] |= 1ull << q.lab[w];
+        P.lab_begin[u] = g.lab_ptr[q.lab[u]];
+        P.lab_end[u] = g.lab_ptr[q.lab[u] + 1];
+    }
     P.greedy = level_plan(q, 0);
-    P.root_begin = g.lab_ptr[q.lab[0]];
-    P.root_end = g.lab_ptr[q.lab[0] + 1];
+    P.root_begin = P.lab_begin[0];
+    P.root_end = P.lab_end[0];
     int orb[MAXN];
     orbits(q, orb);
     int k = 0;
     for (int u = 0; u < q.n; u++) {
         if (orb[u] != u) continue;
-        P.orb[k] = level_plan(q, u);
-        P.orb_begin[k] = g.lab_ptr[q.lab[u]];
-        P.orb_end[k] = g.lab_ptr[q.lab[u] + 1];
+        P.orb[k] = level_plan(q, u);  // orb[k].vert[0] == u
         k++;
     }
     P.n_orb = k;

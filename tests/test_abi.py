@@ -42,8 +42,8 @@ def test_every_declared_symbol_is_exported():
 def test_struct_sizes_match_header():
     import ctypes as C
     assert C.sizeof(fx.flexis_options) == 64
-    assert C.sizeof(fx.flexis_support_result) == 64
-    assert C.sizeof(fx.flexis_plan) == 512
+    assert C.sizeof(fx.flexis_support_result) == 80
+    assert C.sizeof(fx.flexis_plan) == 1024
 
 
 def test_status_strings():
