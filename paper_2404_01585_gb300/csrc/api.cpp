@@ -43,7 +43,7 @@ bool lambda_to_q(double lambda, int64_t *num) {
 // few patterns -> large windows (parallelism has to come from speculation).
 EvalConfig config_for(const flexis_graph *g, int32_t P) {
     EvalConfig c;
-    int wmax = P >= 64 ? 512 : 1024;
+    int wmax = 4096;
     int wmin = std::max(16, std::min(wmax, 16384 / std::max(1, P)));
     if (g->opt.window_max > 0) wmax = g->opt.window_max;
     if (g->opt.window_min > 0) wmin = g->opt.window_min;

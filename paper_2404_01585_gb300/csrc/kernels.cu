@@ -69,7 +69,7 @@ struct PatState {
     unsigned long long mni_cnt[MAXN];
     unsigned long long steps;  // candidate chunks scanned by the greedy searches
     uint32_t max_steps;        // largest chunk count of one greedy search
-    uint32_t pad2;
+    int32_t buf;               // current window buffer (0 or 1)
 };
 
 struct Ctl {
@@ -95,10 +95,10 @@ struct Batch {
     int32_t sel_cap;
     PatState *st;
     uint32_t *used;       // [P][words]
-    int32_t *win_root;    // [P][Wmax]
-    int32_t *win_state;   // [P][Wmax]
-    int32_t *win_map;     // [P][Wmax][8] (by level)
-    int2 *items;          // [P*Wmax]
+    int32_t *win_root;    // [P][2][Wmax]  two window buffers per pattern
+    int32_t *win_state;   // [P][2][Wmax]
+    int32_t *win_map;     // [P][2][Wmax][8] (by level)
+    int2 *items;          // [P*Wmax] (pattern, buffer * Wmax + slot)
     Ctl *ctl;
     int32_t *sel;         // [P][sel_cap][8] selected maps, canonical vertex order
     unsigned long long *mni_seg;  // [P*8+1] prefix sums of MNI candidate segments
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch B, int q) {
         const int p = item.x, s = item.y;
         const Plan &P = B.plans[p];
         load_level_plan(W, P.greedy, P);
-        const size_t slot = (size_t)p * B.Wmax + s;
+        const size_t slot = (size_t)p * 2 * B.Wmax + s;  // s includes the buffer offset
         const int32_t root = B.win_root[slot];
         uint32_t steps = 0;
         const bool found = dfs_first(B.G, W, B.used + (size_t)p * B.G.words, root, bytes, probes, steps);
@@ -418,24 +418,26 @@ __device__ __forceinline__ int block_scan(int v, int &excl, int *sh /* >= 33 int
     return total;
 }
 
-// hash-table capacity of the commit kernel: a power of two >= 2 x (window slots x 8 vertices)
-__host__ __device__ __forceinline__ int hash_slots(int Wmax) {
-    int t = 64;
-    while (t < 2 * Wmax * MAXN) t <<= 1;
-    return t;
-}
+// Map slots one commit examines: bounds the shared-memory inverted index (the window itself
+// can be larger; slots past the horizon are simply kept for the next round).
+constexpr int KMAP = 512;
+constexpr int COMMIT_HASH = 8192;  // power of two >= 2 * KMAP * MAXN
 
 __device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
     return ((uint32_t)v * 0x9E3779B1u) >> (32 - logT);
 }
 
 // One block per pattern: inverted index of the window's maps, prefix commit, refill, new items.
+// The window lives in two global buffers per pattern; the kept slots and the refill go to the
+// other buffer, which becomes current for the next search.
 __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     extern __shared__ int32_t smem[];
+    int32_t *keys = smem, *vals = smem + COMMIT_HASH;
     __shared__ int sh_scan[40];
-    __shared__ int s_f, s_newcur;
+    __shared__ int s_f, s_newcur, s_horizon, s_base;
     const int p = blockIdx.x;
     const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
     if (p == 0 && tid == 0) {
         B.ctl->n_items[q ^ 1] = 0;
         B.ctl->next_item[q ^ 1] = 0;
@@ -447,25 +449,39 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     const int n = P.n;
     const int nwin = S->nwin;
     const int Wmax = B.Wmax;
-    const size_t wbase = (size_t)p * Wmax;
+    const int cur = S->buf, nxt = cur ^ 1;
+    const size_t pb = (size_t)p * 2 * Wmax;
+    const size_t cb = pb + (size_t)cur * Wmax, nb = pb + (size_t)nxt * Wmax;
+    const int32_t *st_cur = B.win_state + cb, *rt_cur = B.win_root + cb, *mp_cur = B.win_map + cb * MAXN;
+    int32_t *st_nxt = B.win_state + nb, *rt_nxt = B.win_root + nb, *mp_nxt = B.win_map + nb * MAXN;
     uint32_t *used = B.used + (size_t)p * B.G.words;
 
-    // shared layout: keys[T] vals[T] | st_root[Wmax] st_state[Wmax] st_map[Wmax*8]
-    int logT = 6;
-    while ((1 << logT) < 2 * nwin * n) logT++;
-    const int T = 1 << logT;
-    const int Tmax = hash_slots(Wmax);
-    int32_t *keys = smem, *vals = smem + Tmax;
-    int32_t *st_root = smem + 2 * Tmax, *st_state = st_root + Wmax, *st_map = st_state + Wmax;
-
-    for (int k = tid; k < T; k += blockDim.x) { keys[k] = -1; vals[k] = INT_MAX; }
-    if (tid == 0) { s_f = nwin; }
+    // 1. horizon: index of the (KMAP+1)-th map slot (or the window end)
+    if (tid == 0) s_horizon = nwin;
     __syncthreads();
-    // 1. inverted index: vertex -> owner (smallest slot whose map holds it)
-    for (int idx = tid; idx < nwin * n; idx += blockDim.x) {
+    int nmap = 0;
+    for (int b0 = 0; b0 < nwin; b0 += nthr) {
+        const int s = b0 + tid;
+        const int ism = (s < nwin && st_cur[s] == SLOT_MAP) ? 1 : 0;
+        int excl;
+        const int tot = block_scan(ism, excl, sh_scan);
+        if (ism && nmap + excl == KMAP) s_horizon = s;
+        nmap += tot;
+    }
+    __syncthreads();
+    const int horizon = s_horizon;
+    const int nins = min(nmap, KMAP) * n;
+    int logT = 6;
+    while ((1 << logT) < 2 * nins) logT++;
+    const int T = 1 << logT;
+    for (int k = tid; k < T; k += nthr) { keys[k] = -1; vals[k] = INT_MAX; }
+    if (tid == 0) s_f = horizon;
+    __syncthreads();
+    // 2. inverted index: vertex -> owner (smallest slot before the horizon whose map holds it)
+    for (int idx = tid; idx < horizon * n; idx += nthr) {
         const int s = idx / n, k = idx - s * n;
-        if (B.win_state[wbase + s] != SLOT_MAP) continue;
-        const int32_t v = B.win_map[(wbase + s) * MAXN + k];
+        if (st_cur[s] != SLOT_MAP) continue;
+        const int32_t v = mp_cur[(size_t)s * MAXN + k];
         uint32_t h = hslot(v, logT);
         for (;;) {
             const int32_t prev = atomicCAS(&keys[h], -1, v);
@@ -474,107 +490,90 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         }
     }
     __syncthreads();
-    // owner lookup (the vertex is present)
-    auto owner = [&](int32_t v) {
+    auto owner = [&](int32_t v) -> int {  // INT_MAX when v is in no indexed map
         uint32_t h = hslot(v, logT);
-        while (keys[h] != v) h = (h + 1) & (T - 1);
-        return vals[h];
+        for (;;) {
+            const int32_t k = keys[h];
+            if (k == v) return vals[h];
+            if (k == -1) return INT_MAX;
+            h = (h + 1) & (T - 1);
+        }
     };
-    // 2. first slot whose map meets an earlier slot's map
-    for (int idx = tid; idx < nwin * n; idx += blockDim.x) {
+    // 3. first slot whose map meets an earlier slot's map
+    for (int idx = tid; idx < horizon * n; idx += nthr) {
         const int s = idx / n, k = idx - s * n;
-        if (B.win_state[wbase + s] != SLOT_MAP) continue;
-        if (owner(B.win_map[(wbase + s) * MAXN + k]) < s) atomicMin(&s_f, s);
+        if (st_cur[s] != SLOT_MAP) continue;
+        if (owner(mp_cur[(size_t)s * MAXN + k]) < s) atomicMin(&s_f, s);
     }
     __syncthreads();
     const int f = s_f;
-    // 3. commit the map slots before f, in slot order
-    int64_t count0 = S->count;
+    // 4. commit the map slots before f, in slot order
+    const int64_t count0 = S->count;
     int ncommit = 0;
-    {
-        const int per = (nwin + blockDim.x - 1) / blockDim.x;
-        int mine = 0;
-        for (int k = 0; k < per; k++) {
-            const int s = tid * per + k;
-            if (s < nwin && s < f && B.win_state[wbase + s] == SLOT_MAP) mine++;
-        }
+    for (int b0 = 0; b0 < f; b0 += nthr) {
+        const int s = b0 + tid;
+        const int isc = (s < f && st_cur[s] == SLOT_MAP) ? 1 : 0;
         int excl;
-        ncommit = block_scan(mine, excl, sh_scan);
-        int r = excl;
-        for (int k = 0; k < per; k++) {
-            const int s = tid * per + k;
-            if (!(s < nwin && s < f && B.win_state[wbase + s] == SLOT_MAP)) continue;
-            const int32_t *m = B.win_map + (wbase + s) * MAXN;
+        const int tot = block_scan(isc, excl, sh_scan);
+        if (isc) {
+            const int32_t *m = mp_cur + (size_t)s * MAXN;
             for (int l = 0; l < n; l++) atomicOr(used + (m[l] >> 5), 1u << (m[l] & 31));
-            const int64_t at = count0 + r;
+            const int64_t at = count0 + ncommit + excl;
             if (B.sel && at < B.sel_cap && at < P.cap) {
                 int32_t *o = B.sel + ((size_t)p * B.sel_cap + at) * MAXN;
                 for (int l = 0; l < n; l++) o[P.greedy.vert[l]] = m[l];
             }
-            r++;
         }
+        ncommit += tot;
     }
-    // 4. keep the slots from f on that still matter; a kept map needs a new search if a
-    //    committed map took one of its vertices
-    int keep_n;
-    {
-        const int per = (nwin + blockDim.x - 1) / blockDim.x;
-        int mine = 0;
-        int flag[8];
-        for (int k = 0; k < per && k < 8; k++) {
-            const int s = tid * per + k;
-            flag[k] = (s < nwin && s >= f && B.win_state[wbase + s] != SLOT_NONE) ? 1 : 0;
-            mine += flag[k];
-        }
+    __syncthreads();  // the used bits of step 4 are read by the refill of step 7
+    // 5. keep the slots from f on that still matter, in order, in the other buffer; a kept map
+    //    needs a new search if a committed map took one of its vertices
+    int keep_n = 0;
+    for (int b0 = f; b0 < nwin; b0 += nthr) {
+        const int s = b0 + tid;
+        const int kp = (s < nwin && st_cur[s] != SLOT_NONE) ? 1 : 0;
         int excl;
-        keep_n = block_scan(mine, excl, sh_scan);
-        int r = excl;
-        for (int k = 0; k < per && k < 8; k++) {
-            if (!flag[k]) continue;
-            const int s = tid * per + k;
-            int state = B.win_state[wbase + s];
+        const int tot = block_scan(kp, excl, sh_scan);
+        if (kp) {
+            const int r = keep_n + excl;
+            int state = st_cur[s];
             if (state == SLOT_MAP) {
-                const int32_t *m = B.win_map + (wbase + s) * MAXN;
-                for (int l = 0; l < n; l++)
-                    if (owner(m[l]) < f) { state = SLOT_NEEDS; break; }
-                for (int l = 0; l < MAXN; l++) st_map[r * MAXN + l] = m[l];
+                const int32_t *m = mp_cur + (size_t)s * MAXN;
+                for (int l = 0; l < n; l++) {
+                    mp_nxt[(size_t)r * MAXN + l] = m[l];
+                    if (owner(m[l]) < f) state = SLOT_NEEDS;
+                }
             }
-            st_root[r] = B.win_root[wbase + s];
-            st_state[r] = state;
-            r++;
+            rt_nxt[r] = rt_cur[s];
+            st_nxt[r] = state;
         }
+        keep_n += tot;
     }
-    __syncthreads();
-    for (int s = tid; s < keep_n; s += blockDim.x) {
-        B.win_root[wbase + s] = st_root[s];
-        B.win_state[wbase + s] = st_state[s];
-        for (int l = 0; l < MAXN; l++) B.win_map[(wbase + s) * MAXN + l] = st_map[s * MAXN + l];
-    }
-    // 5. window size: grow while speculation is conflict-free
+    // 6. window size: grow while speculation is conflict-free
     int W = S->W;
     if (nwin > 0 && f >= nwin) W = min(2 * W, Wmax);
-    // 6. refill from the root order, skipping roots already used
+    // 7. refill from the root order; a used root, or one that cannot host canonical vertex 0,
+    //    has no map and is decided on the spot
     int nw = keep_n;
     int cursor = S->cursor;
     const int rend = P.root_end;
-    __syncthreads();
     while (nw < W && cursor < rend) {
-        const int chunk = min((int)blockDim.x, rend - cursor);
+        const int chunk = min(nthr, rend - cursor);
         const int need = W - nw;
         int ok = 0;
         int32_t r = -1;
         if (tid < chunk) {
             r = __ldg(B.G.lab_vtx + cursor + tid);
-            // a used root, or one that cannot host canonical vertex 0, has no map: decided now
             ok = (!used_bit(used, r) && vertex_fits(B.G, r, P.greedy.deg[0], P.need[0])) ? 1 : 0;
         }
-        if (tid == 0) { s_newcur = cursor + chunk; }
+        if (tid == 0) s_newcur = cursor + chunk;
         __syncthreads();
         int excl;
         const int tot = block_scan(ok, excl, sh_scan);
         if (ok && excl < need) {
-            B.win_root[wbase + nw + excl] = r;
-            B.win_state[wbase + nw + excl] = SLOT_NEEDS;
+            rt_nxt[nw + excl] = r;
+            st_nxt[nw + excl] = SLOT_NEEDS;
             if (excl == need - 1) s_newcur = cursor + tid + 1;
         }
         __syncthreads();
@@ -582,45 +581,45 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         cursor = s_newcur;
         __syncthreads();
     }
-    // 7. emit search items for every slot that needs a map
-    {
-        const int per = (nw + blockDim.x - 1) / blockDim.x;
-        int mine = 0;
-        for (int k = 0; k < per; k++) {
-            const int s = tid * per + k;
-            if (s < nw && B.win_state[wbase + s] == SLOT_NEEDS) mine++;
-        }
-        __syncthreads();
+    // 8. one search item for every slot that needs a map
+    __syncthreads();
+    int nitems = 0;
+    for (int b0 = 0; b0 < nw; b0 += nthr) {
+        const int s = b0 + tid;
         int excl;
-        const int tot = block_scan(mine, excl, sh_scan);
-        __shared__ int s_base;
-        if (tid == 0) s_base = tot ? atomicAdd(&B.ctl->n_items[q], tot) : 0;
-        __syncthreads();
-        int r = s_base + excl;
-        for (int k = 0; k < per; k++) {
-            const int s = tid * per + k;
-            if (s < nw && B.win_state[wbase + s] == SLOT_NEEDS) B.items[r++] = make_int2(p, s);
+        nitems += block_scan((s < nw && st_nxt[s] == SLOT_NEEDS) ? 1 : 0, excl, sh_scan);
+    }
+    if (tid == 0) s_base = nitems ? atomicAdd(&B.ctl->n_items[q], nitems) : 0;
+    __syncthreads();
+    int wr = s_base;
+    for (int b0 = 0; b0 < nw; b0 += nthr) {
+        const int s = b0 + tid;
+        const int nd = (s < nw && st_nxt[s] == SLOT_NEEDS) ? 1 : 0;
+        int excl;
+        const int tot = block_scan(nd, excl, sh_scan);
+        if (nd) B.items[wr + excl] = make_int2(p, nxt * Wmax + s);
+        wr += tot;
+    }
+    if (tid == 0) {
+        const int64_t count = count0 + ncommit;
+        S->count = count;
+        if (B.sel) S->logged = (int32_t)min(min(count, P.cap), (int64_t)B.sel_cap);
+        S->buf = nxt;
+        S->cursor = cursor;
+        S->nwin = nw;
+        S->W = W;
+        S->rounds++;
+        S->searched += nitems;
+        const bool reached = count >= P.cap;
+        const bool exhausted = nw == 0 && cursor >= rend;
+        if (reached || exhausted) {
+            S->done = 1;
+            S->exhausted = exhausted && !reached;
+            S->phase = PH_MNI;
+        } else {
+            atomicAdd(&B.ctl->active[q], 1);
         }
-        if (tid == 0) {
-            const int64_t count = count0 + ncommit;
-            S->count = count;
-            if (B.sel) S->logged = (int32_t)min(min(count, P.cap), (int64_t)B.sel_cap);
-            S->cursor = cursor;
-            S->nwin = nw;
-            S->W = W;
-            S->rounds++;
-            S->searched += tot;
-            const bool reached = count >= P.cap;
-            const bool exhausted = nw == 0 && cursor >= rend;
-            if (reached || exhausted) {
-                S->done = 1;
-                S->exhausted = exhausted && !reached;
-                S->phase = PH_MNI;
-            } else {
-                atomicAdd(&B.ctl->active[q], 1);
-            }
-            if (tot) atomicAdd(&B.ctl->search_items, (unsigned long long)tot);
-        }
+        if (nitems) atomicAdd(&B.ctl->search_items, (unsigned long long)nitems);
     }
 }
 
@@ -803,9 +802,7 @@ static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &by
     return FLEXIS_OK;
 }
 
-static size_t commit_smem(int Wmax) {
-    return sizeof(int32_t) * ((size_t)2 * hash_slots(Wmax) + (size_t)Wmax * (2 + MAXN));
-}
+static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
     int ndev = 0;
@@ -832,7 +829,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
         cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)
         return fail(FLEXIS_E_CUDA);
     if (cudaFuncSetAttribute(k_commit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)commit_smem(1024)) != cudaSuccess)
+                             (int)commit_smem(0)) != cudaSuccess)
         return fail(FLEXIS_E_CUDA);
     *out = g;
     return FLEXIS_OK;
@@ -854,9 +851,9 @@ static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax
     CK(cudaMalloc(&w.st, sizeof(PatState) * nP));
     CK(cudaMemset(w.st, 0, sizeof(PatState) * nP));
     CK(cudaMalloc(&w.used, sizeof(uint32_t) * words * nP));
-    CK(cudaMalloc(&w.win_root, sizeof(int32_t) * (size_t)nP * nW));
-    CK(cudaMalloc(&w.win_state, sizeof(int32_t) * (size_t)nP * nW));
-    CK(cudaMalloc(&w.win_map, sizeof(int32_t) * (size_t)nP * nW * MAXN));
+    CK(cudaMalloc(&w.win_root, sizeof(int32_t) * (size_t)nP * nW * 2));
+    CK(cudaMalloc(&w.win_state, sizeof(int32_t) * (size_t)nP * nW * 2));
+    CK(cudaMalloc(&w.win_map, sizeof(int32_t) * (size_t)nP * nW * 2 * MAXN));
     CK(cudaMalloc(&w.items, sizeof(int2) * (size_t)nP * nW));
     CK(cudaMalloc(&w.ctl, sizeof(Ctl)));
     CK(cudaMalloc(&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
@@ -925,7 +922,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
              cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats) {
     if (P <= 0) return FLEXIS_OK;
     CK(cudaSetDevice(g->device));
-    const int Wmax = std::max(32, std::min(cfg.w_max, 1024));
+    const int Wmax = std::max(32, std::min(cfg.w_max, 16384));
     const int Wmin = std::max(1, std::min(cfg.w_min, Wmax));
     int rc = ws_ensure(g, g->ws, P, Wmax, cfg.record_selected);
     if (rc) return rc;
@@ -1021,7 +1018,7 @@ int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support
     if (P <= 0) return FLEXIS_OK;
     CK(cudaSetDevice(g->device));
     Workspace &w = g->ws;
-    int rc = ws_ensure(g, w, P, std::max(32, std::min(cfg.w_max, 1024)), cfg.record_selected);
+    int rc = ws_ensure(g, w, P, std::max(32, std::min(cfg.w_max, 16384)), cfg.record_selected);
     if (rc) return rc;
     CK(cudaMemcpyAsync(w.plans, h_plans, sizeof(Plan) * (size_t)P, cudaMemcpyHostToDevice, g->stream));
     rc = dev_eval(g, w.plans, P, w.results, g->stream, cfg, stats);
@@ -1055,7 +1052,7 @@ struct ServeSession {
     Workspace w;
     cudaStream_t stream = nullptr;
     int32_t slots = 0;
-    int Wmin = 32, Wmax = 512;
+    int Wmin = 32, Wmax = 2048;
     int32_t *d_admit = nullptr;
     int32_t *h_admit = nullptr;  // pinned
     Plan *h_plans = nullptr;     // pinned staging
@@ -1107,7 +1104,8 @@ void serve_destroy(ServeSession *s) {
 }
 
 int serve_slot_bytes(const DeviceGraph *g, int64_t *bytes) {
-    *bytes = (int64_t)g->view.words * 4 + 512ll * (4 + 4 + 4 * MAXN + 8) + (int64_t)sizeof(PatState) +
+    const int64_t W = ServeSession().Wmax;
+    *bytes = (int64_t)g->view.words * 4 + W * (2 * (4 + 4 + 4 * MAXN) + 8) + (int64_t)sizeof(PatState) +
              (int64_t)sizeof(Plan);
     return FLEXIS_OK;
 }
