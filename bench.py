@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: candidate supports evaluated per second, FLEXIS frequent subgraph mining on GB300.
+
+Workload (one step): the MiCo-shaped mining sweep -- a seeded Chung-Lu graph (exponent 2.3,
+100,000 vertices, 1,080,000 undirected edges, 29 vertex labels Zipf(1.2)); Algorithm 1 mining of
+all connected patterns with up to 5 edges, once per (sigma, lambda) of the sweep.  Every
+candidate the mining loop evaluates (all levels, all runs) counts as one support evaluation.
+
+  value : supports/s through flexis_mine with the graph already resident on the device
+          (CUDA events on the library's stream around the K timed steps; L2 flushed between
+          steps by a 256 MiB write).
+  e2e   : the same metric through the public API from host buffers: every step loads the graph
+          from host arrays (flexis_load_graph), mines, reads the frequent sets back.
+  roofline : the dominant kernel (the greedy search kernel), algorithmic bytes counted by the
+          kernel itself / its summed CUDA-event time, against the measured HBM copy bandwidth.
+  cpu_baseline : the plain C oracle, single thread, on a bounded sample of the same workload.
+  batched_vs_plain : 256 candidates of the sweep evaluated in one batch vs one call each.
+
+`python bench.py --impl reference` times the oracle instead (the reference arm of this build is
+its CPU oracle).  N > 1 (torchrun): independent replicas, one per GPU (the evaluation path has no
+exchange step); value = all ranks' supports / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP = [(1000, 0.5), (2000, 0.5), (3000, 0.5), (1000, 1.0), (2000, 1.0), (3000, 1.0)]
+MAX_EDGES = 5
+METRIC = "candidate supports evaluated/sec (bit-exact vs oracle), batched vs plain on 1 GB300; p50/p99"
+UNIT = "supports/s"
+# oracle sample: the same graph and sweep, mining limited to 3 edges (levels 2..4)
+ORACLE_SAMPLE = dict(runs=[(3000, 0.5), (3000, 1.0)], max_edges=3)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_inputs():
+    from workloads import make_graph
+    return make_graph("mico")
+
+
+def config_dict(extra=None):
+    d = {"workload": "MiCo-shaped mining sweep (configs[1]): Chung-Lu gamma=2.3, 100000 v, "
+                     "1080000 e, 29 labels Zipf(1.2); patterns up to 5 edges",
+         "sweep_sigma_lambda": SWEEP, "max_edges": MAX_EDGES, "mode": "EARLY (stop at tau), mIS decision",
+         "l2": "flushed between steps (256 MiB device write)", "graph_seed": 1002}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def run_oracle_sample(lab, src, dst):
+    """The oracle as it stands, single-threaded, on the bounded sample; returns
+    (supports, seconds, description)."""
+    import oracle
+    oracle.build()
+    g = oracle.Graph(lab, src, dst)
+    t0 = time.perf_counter()
+    cand = 0
+    for sigma, lam in ORACLE_SAMPLE["runs"]:
+        _, levels = g.mine(sigma=sigma, lam=lam, max_edges=ORACLE_SAMPLE["max_edges"])
+        cand += sum(c for c, _ in levels.values())
+    dt = time.perf_counter() - t0
+    desc = (f"oracle tier-1 mining of the same graph, (sigma, lambda) in {ORACLE_SAMPLE['runs']}, "
+            f"max_edges={ORACLE_SAMPLE['max_edges']} (levels 2..4): {cand} supports")
+    return cand, dt, desc
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    lab, src, dst = load_inputs()
+    for _ in range(args.warmup):
+        run_oracle_sample(lab, src, dst)
+    tot_c, tot_t, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        c, t, desc = run_oracle_sample(lab, src, dst)
+        tot_c += c
+        tot_t += t
+    v = tot_c / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_dict({"reference": "plain C oracle (CPU)"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="SIGMA,LAMBDA: time one mining run instead of the sweep (profiling)")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the e2e, batched-vs-plain and CPU-baseline legs (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    global SWEEP
+    if args.only:
+        s, l = args.only.split(",")
+        SWEEP = [(int(s), float(l))]
+    if args.skip_extras:
+        args.no_cpu_baseline = True
+
+    import torch
+    import paper_2404_01585_gb300 as fx
+    import __graft_entry__
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+
+    lab, src, dst = load_inputs()
+    g = fx.Graph(lab, src, dst, device=local, timing=True)
+    ext = torch.cuda.ExternalStream(g.stream(), device=local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def step():
+        cand, freq = 0, 0
+        acc = {}
+        for sigma, lam in SWEEP:
+            pats, levels = g.mine(sigma, lam, MAX_EDGES)
+            cand += sum(c for c, _ in levels.values())
+            freq += len(pats)
+            st = g.stats()
+            for k, v in st.items():
+                acc[k] = acc.get(k, 0) + v
+        return cand, freq, acc
+
+    for _ in range(args.warmup):
+        step()
+    # timed region
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(ext)
+    total_c, stats = 0, {}
+    for k in range(args.steps):
+        if k:
+            flush.zero_()
+            torch.cuda.synchronize()
+        c, f, acc = step()
+        total_c += c
+        for kk, v in acc.items():
+            stats[kk] = stats.get(kk, 0) + v
+    ev1.record(ext)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t_max = ms
+    c_all = total_c
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        cc = torch.tensor([total_c], dtype=torch.float64)
+        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+        c_all = int(cc.item())
+    value = c_all / (t_max / 1e3)
+
+    # roofline of the greedy search kernel
+    peak, peak_kind = peaks()
+    search_s = stats["search_ms"] / 1e3
+    achieved = stats["alg_bytes_greedy"] / search_s / 1e9 if search_s > 0 else 0.0
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_search (greedy root search)", "peak_kind": peak_kind,
+                "search_ms_share": stats["search_ms"] / ms if ms else None}
+
+    # e2e through the public API from host buffers: load + mine + read back, every step
+    e2e_c, e2e_t, h2d, d2h = 0, 0.0, 0, 0
+    for k in range(0 if args.skip_extras else args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = fx.Graph(lab, src, dst, device=local)
+        info = g2.info()
+        for sigma, lam in SWEEP:
+            pats, levels = g2.mine(sigma, lam, MAX_EDGES)
+            e2e_c += sum(c for c, _ in levels.values())
+            st = g2.stats()
+            h2d += st["h2d_bytes"]
+            d2h += st["d2h_bytes"] + 80 * len(pats)
+        h2d += info["device_bytes"]
+        g2.close()
+        torch.cuda.synchronize()
+        e2e_t += time.perf_counter() - t0
+    e2e = None if args.skip_extras else {
+        "value": e2e_c / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+        "d2h_bytes_per_step": d2h // args.steps}
+
+    # batched vs plain on a sample of the sweep's candidates
+    pats, levels = g.mine(2000, 0.5, 4) if not args.skip_extras else ([], {})
+    sample = [(p["labels"], p["edges"]) for p in pats if p["n"] >= 4][:256]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if sample:
+        g.support_batch(sample, 2000, 0.5, fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI)
+    t_batch = time.perf_counter() - t0
+    lat = []
+    for lb, ed in sample:
+        t1 = time.perf_counter()
+        g.support(lb, ed, 2000, 0.5, mode=fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI)
+        lat.append(time.perf_counter() - t1)
+    lat.sort()
+    bvp = None if not sample else {"sample": f"{len(sample)} frequent 4-5 vertex patterns of sigma=2000, lambda=0.5",
+           "batched_supports_per_s": len(sample) / t_batch,
+           "plain_supports_per_s": len(sample) / sum(lat),
+           "plain_p50_ms": 1e3 * lat[len(lat) // 2], "plain_p99_ms": 1e3 * lat[min(len(lat) - 1, int(len(lat) * 0.99))]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c, t, desc = run_oracle_sample(lab, src, dst)
+        cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": t}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                       "supports_per_step": total_c // args.steps}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(stats.get("kernel_launches", 0)), "clocks": clk,
+                "batched_vs_plain": bvp,
+                "kernel_time_ms": {"search": stats["search_ms"], "device_total": stats["total_ms"],
+                                   "host_candidate_generation": stats["host_gen_ms"],
+                                   "host_compile": stats["host_compile_ms"]}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    g.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

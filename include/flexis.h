@@ -141,10 +141,16 @@ typedef struct {
     int64_t alg_bytes;        /* algorithmic bytes read by the search kernels (adjacency entries,
                                  label-run entries, vertex records, used-bitmap words) */
     int64_t alg_bytes_greedy; /* part of alg_bytes read by the greedy search kernel */
+    int64_t patterns;         /* patterns evaluated by the call */
+    int64_t h2d_bytes;        /* bytes copied host -> device (plans) */
+    int64_t d2h_bytes;        /* bytes copied device -> host (results, control words) */
     float search_ms;          /* summed CUDA-event time of the greedy search kernel launches */
     float mni_ms;             /* CUDA-event time of the MNI kernel */
-    float total_ms;           /* CUDA-event time of the whole device section */
+    float total_ms;           /* CUDA-event time of the device sections */
+    float host_gen_ms;        /* host time in candidate generation (mining) */
+    float host_compile_ms;    /* host time in pattern compilation */
     int32_t search_launches;  /* launches of the greedy search kernel */
+    int32_t batches;          /* device batches (memory-admitted chunks of the patterns) */
     int32_t pad;
 } flexis_stats;
 
@@ -197,6 +203,10 @@ int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int
 
 /* Counters of the last evaluation call on g. */
 int flexis_last_stats(const flexis_graph *g, flexis_stats *out);
+
+/* The CUDA stream (a cudaStream_t) on which g's evaluations run, for callers that time them
+ * with CUDA events or order their own work after them.  Owned by the graph.                    */
+void *flexis_graph_stream(const flexis_graph *g);
 
 /* Selected maps recorded by the last evaluation when opt.record_selected > 0: for pattern i,
  * up to `cap` maps of 8 ids each (canonical-vertex order, in selection order) into maps_out;

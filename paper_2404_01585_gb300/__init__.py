@@ -79,8 +79,10 @@ class flexis_graph_info(C.Structure):
 class flexis_stats(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("search_items", C.c_int64), ("mni_items", C.c_int64),
                 ("kernel_launches", C.c_int64), ("alg_bytes", C.c_int64),
-                ("alg_bytes_greedy", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
-                ("total_ms", C.c_float), ("search_launches", C.c_int32), ("pad", C.c_int32)]
+                ("alg_bytes_greedy", C.c_int64), ("patterns", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
+                ("total_ms", C.c_float), ("host_gen_ms", C.c_float), ("host_compile_ms", C.c_float),
+                ("search_launches", C.c_int32), ("batches", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
@@ -107,6 +109,7 @@ SYMBOLS = {
                                   C.c_int32, C.POINTER(flexis_plan)]),
     "flexis_support_plans_device": (C.c_int, [_P, _P, C.c_int32, _P, _P]),
     "flexis_last_stats": (C.c_int, [_P, C.POINTER(flexis_stats)]),
+    "flexis_graph_stream": (C.c_void_p, [_P]),
     "flexis_selected_maps": (C.c_int, [_P, C.c_int32, _I32P, C.c_int64, _I64P]),
     "flexis_mine": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int32, C.POINTER(_P)]),
     "flexis_pattern_set_count": (C.c_int64, [_P]),
@@ -269,6 +272,10 @@ class Graph:
         rc = lib().flexis_support_plans_device(self._h, C.c_void_p(d_plans_ptr), count,
                                                C.c_void_p(d_results_ptr), C.c_void_p(stream_ptr))
         _check(rc, "flexis_support_plans_device")
+
+    def stream(self) -> int:
+        """cudaStream_t (as an int) on which this graph's evaluations run."""
+        return int(lib().flexis_graph_stream(self._h) or 0)
 
     def stats(self) -> dict:
         s = flexis_stats()

@@ -1,5 +1,6 @@
 // C ABI of the FLEXIS GB300 library (declared in include/flexis.h).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -39,11 +40,50 @@ bool lambda_to_q(double lambda, int64_t *num) {
     return true;
 }
 
-// Autotuned launch shape: many patterns -> small windows (parallelism comes from the batch);
-// few patterns -> large windows (parallelism has to come from speculation).
+using Clock = std::chrono::steady_clock;
+
+float ms_since(Clock::time_point t0) {
+    return std::chrono::duration<float, std::milli>(Clock::now() - t0).count();
+}
+
+int host_threads() { return (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency())); }
+
+template <class F>
+void parallel_chunks(int64_t n, int T, F f) {
+    if (n < 256) T = 1;
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + T - 1) / T;
+    for (int t = 1; t < T; t++) {
+        const int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+        if (lo < hi) th.emplace_back([=] { f(lo, hi); });
+    }
+    f(0, std::min(n, chunk));
+    for (auto &x : th) x.join();
+}
+
+void add_stats(flexis_stats &a, const flexis_stats &b) {
+    a.rounds += b.rounds;
+    a.search_items += b.search_items;
+    a.mni_items += b.mni_items;
+    a.kernel_launches += b.kernel_launches;
+    a.alg_bytes += b.alg_bytes;
+    a.alg_bytes_greedy += b.alg_bytes_greedy;
+    a.patterns += b.patterns;
+    a.search_ms += b.search_ms;
+    a.mni_ms += b.mni_ms;
+    a.total_ms += b.total_ms;
+    a.host_gen_ms += b.host_gen_ms;
+    a.host_compile_ms += b.host_compile_ms;
+    a.search_launches += b.search_launches;
+    a.batches += b.batches;
+}
+
+// Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism
+// comes from the batch, and per-pattern window memory stays small); few patterns -> large
+// windows (parallelism has to come from speculation inside each pattern).
 EvalConfig config_for(const flexis_graph *g, int32_t P) {
     EvalConfig c;
-    int wmax = 4096;
+    int wmax = P < 64 ? 8192 : P < 4096 ? 4096 : P < 65536 ? 1024 : 512;
     int wmin = std::max(16, std::min(wmax, 16384 / std::max(1, P)));
     if (g->opt.window_max > 0) wmax = g->opt.window_max;
     if (g->opt.window_min > 0) wmin = g->opt.window_min;
@@ -56,9 +96,29 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     return c;
 }
 
+// Memory-admitted batches: the device workspace of one batch (used bitmaps, windows, items) is
+// bounded by a share of the free device memory; larger candidate sets run as several batches.
 int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result *out) {
-    EvalConfig cfg = config_for(g, (int32_t)plans.size());
-    return dev_eval_host(g->dg, plans.data(), (int32_t)plans.size(), out, cfg, &g->last);
+    const int64_t P = (int64_t)plans.size();
+    EvalConfig cfg = config_for(g, (int32_t)std::min<int64_t>(P, INT32_MAX));
+    int64_t per = 1, fr = 0;
+    dev_pattern_bytes(g->dg, cfg.w_max, cfg.record_selected, &per);
+    dev_free_bytes(g->dg, &fr);
+    const int64_t budget = std::max<int64_t>(fr / 3, 256ll << 20);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({P, budget / std::max<int64_t>(per, 1), 1 << 22}));
+    flexis_stats total{};
+    for (int64_t lo = 0; lo < P; lo += chunk) {
+        const int32_t cnt = (int32_t)std::min(chunk, P - lo);
+        EvalConfig c2 = config_for(g, cnt);
+        flexis_stats st{};
+        int rc = dev_eval_host(g->dg, plans.data() + lo, cnt, out + lo, c2, &st);
+        if (rc) return rc;
+        st.patterns = cnt;
+        st.batches = 1;
+        add_stats(total, st);
+    }
+    g->last = total;
+    return FLEXIS_OK;
 }
 
 void pattern_of_code(const flexis_graph *g, const Code &c, std::vector<int32_t> &labels,
@@ -216,6 +276,8 @@ int flexis_last_stats(const flexis_graph *g, flexis_stats *out) {
     return FLEXIS_OK;
 }
 
+void *flexis_graph_stream(const flexis_graph *g) { return g ? (void *)dev_graph_stream(g->dg) : nullptr; }
+
 int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,
                          int64_t *n_out) {
     if (!g || !maps_out || !n_out || cap < 0) return FLEXIS_E_INVALID;
@@ -239,20 +301,24 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
         C.push_back(c);
     }
     std::sort(C.begin(), C.end());
-    int threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int threads = host_threads();
+    flexis_stats total{};
     for (int k = 2; k <= max_edges + 1 && k <= FLEXIS_MAX_PATTERN && !C.empty(); k++) {
         S->cand[k] = (int64_t)C.size();
         std::vector<Plan> plans(C.size());
-        std::vector<int32_t> labels, edges;
-        for (size_t i = 0; i < C.size(); i++) {
-            pattern_of_code(g, C[i], labels, edges);
-            flexis_pattern p{(int32_t)labels.size(), (int32_t)(edges.size() / 2), labels.data(), edges.data()};
-            // the metric step of Algorithm 1 needs the mIS decision only (Sec. 3.2.2)
-            compile_plan(g->hg, p, sigma, num, LAMBDA_DEN, FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI, plans[i]);
-        }
+        auto t0 = Clock::now();
+        // candidates are canonical codes over label ranks already; the metric step of
+        // Algorithm 1 needs the mIS decision only (Sec. 3.2.2)
+        parallel_chunks((int64_t)C.size(), threads, [&](int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; i++)
+                compile_code(g->hg, C[(size_t)i], sigma, num, LAMBDA_DEN,
+                             FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI, plans[(size_t)i]);
+        });
+        total.host_compile_ms += ms_since(t0);
         std::vector<flexis_support_result> res(C.size());
         int rc = eval_plans(g, plans, res.data());
         if (rc) return rc;
+        add_stats(total, g->last);
         std::vector<Code> F;
         for (size_t i = 0; i < C.size(); i++)
             if (res[i].status == FLEXIS_OK && res[i].frequent) {
@@ -264,8 +330,11 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
             }
         S->freq[k] = (int64_t)F.size();
         C.clear();
+        t0 = Clock::now();
         if (k + 1 <= max_edges + 1 && k + 1 <= FLEXIS_MAX_PATTERN) generate_candidates(F, max_edges, C, threads);
+        total.host_gen_ms += ms_since(t0);
     }
+    g->last = total;
     *out = S.release();
     return FLEXIS_OK;
 }

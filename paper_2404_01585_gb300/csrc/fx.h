@@ -119,6 +119,9 @@ void orbits(const Pat &p, int *orb);
 LevelPlan level_plan(const Pat &q, int first);
 
 // pattern compile: labels as graph label ids
+void fill_plan(const HostGraph &g, const Code &code, Plan &P);
+int compile_code(const HostGraph &g, const Code &code, int64_t sigma, int64_t lam_num,
+                 int64_t lam_den, int mode, Plan &P);
 int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, int64_t lam_num,
                  int64_t lam_den, int mode, Plan &out);
 int64_t tau_exact(int64_t sigma, int64_t lam_num, int64_t lam_den, int n);

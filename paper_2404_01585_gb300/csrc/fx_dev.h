@@ -36,6 +36,11 @@ int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support
 // Selected maps of pattern i recorded by the last evaluation (cfg.record_selected > 0).
 int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int64_t *n_out);
 
+// Device bytes one pattern of a batch holds (used bitmap, two window buffers, items, state,
+// plan, result); and the device's free memory.
+int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes);
+int dev_free_bytes(const DeviceGraph *g, int64_t *bytes);
+
 // Serving session: `slots` pattern slots on the graph's device with their own workspace.
 struct ServeSession;
 int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out);

@@ -766,7 +766,10 @@ __global__ void k_finalize(Batch B) {
 
 // Evaluation workspace: P pattern slots with their used bitmaps, windows and work items.
 struct Workspace {
-    int32_t P = 0, W = 0, sel = 0;
+    int32_t P = 0;           // pattern capacity
+    int64_t slots = 0;       // window-slot capacity (patterns x window size)
+    int64_t sel_slots = 0;   // selection-log capacity (patterns x maps)
+    int64_t bytes = 0;       // device bytes held
     PatState *st = nullptr;
     uint32_t *used = nullptr;
     int32_t *win_root = nullptr, *win_state = nullptr, *win_map = nullptr;
@@ -803,6 +806,21 @@ static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &by
 }
 
 static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
+
+int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes) {
+    *bytes = (int64_t)g->view.words * 4 + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) +
+             (int64_t)sizeof(PatState) + (int64_t)sizeof(Plan) + (int64_t)sizeof(flexis_support_result) +
+             8 * (MAXN + 1) + (int64_t)sel * 4 * MAXN;
+    return FLEXIS_OK;
+}
+
+int dev_free_bytes(const DeviceGraph *g, int64_t *bytes) {
+    size_t fr = 0, tot = 0;
+    CK(cudaSetDevice(g->device));
+    CK(cudaMemGetInfo(&fr, &tot));
+    *bytes = (int64_t)std::min(fr + (size_t)g->ws.bytes, tot);  // free + what the workspace holds
+    return FLEXIS_OK;
+}
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
     int ndev = 0;
@@ -843,27 +861,39 @@ static void ws_free(Workspace &w) {
     w = Workspace();
 }
 
+// Capacity is kept in patterns and in window slots (patterns x Wmax) separately, so a large
+// batch with small windows followed by a small batch with large windows never allocates the
+// product of the two.
 static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax, int32_t sel) {
-    if (P <= w.P && Wmax <= w.W && sel <= w.sel && w.h_ctl) return FLEXIS_OK;
-    const int32_t nP = std::max(P, w.P), nW = std::max(Wmax, w.W), nS = std::max(sel, w.sel);
+    const int64_t slots = (int64_t)P * Wmax;
+    if (P <= w.P && slots <= w.slots && (int64_t)P * sel <= w.sel_slots && w.h_ctl) return FLEXIS_OK;
+    const int32_t nP = std::max(P, w.P);
+    const int64_t nSlots = std::max(slots, w.slots);
+    const int64_t nSel = std::max((int64_t)P * sel, w.sel_slots);
     ws_free(w);
     const size_t words = (size_t)g->view.words;
-    CK(cudaMalloc(&w.st, sizeof(PatState) * nP));
+    int64_t b = 0;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        b += (int64_t)bytes;
+        return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    };
+    CK(alloc((void **)&w.st, sizeof(PatState) * nP));
     CK(cudaMemset(w.st, 0, sizeof(PatState) * nP));
-    CK(cudaMalloc(&w.used, sizeof(uint32_t) * words * nP));
-    CK(cudaMalloc(&w.win_root, sizeof(int32_t) * (size_t)nP * nW * 2));
-    CK(cudaMalloc(&w.win_state, sizeof(int32_t) * (size_t)nP * nW * 2));
-    CK(cudaMalloc(&w.win_map, sizeof(int32_t) * (size_t)nP * nW * 2 * MAXN));
-    CK(cudaMalloc(&w.items, sizeof(int2) * (size_t)nP * nW));
-    CK(cudaMalloc(&w.ctl, sizeof(Ctl)));
-    CK(cudaMalloc(&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
-    CK(cudaMalloc(&w.plans, sizeof(Plan) * (size_t)nP));
-    CK(cudaMalloc(&w.results, sizeof(flexis_support_result) * (size_t)nP));
-    if (nS > 0) CK(cudaMalloc(&w.sel_buf, sizeof(int32_t) * (size_t)nP * nS * MAXN));
+    CK(alloc((void **)&w.used, sizeof(uint32_t) * words * nP));
+    CK(alloc((void **)&w.win_root, sizeof(int32_t) * (size_t)nSlots * 2));
+    CK(alloc((void **)&w.win_state, sizeof(int32_t) * (size_t)nSlots * 2));
+    CK(alloc((void **)&w.win_map, sizeof(int32_t) * (size_t)nSlots * 2 * MAXN));
+    CK(alloc((void **)&w.items, sizeof(int2) * (size_t)nSlots));
+    CK(alloc((void **)&w.ctl, sizeof(Ctl)));
+    CK(alloc((void **)&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
+    CK(alloc((void **)&w.plans, sizeof(Plan) * (size_t)nP));
+    CK(alloc((void **)&w.results, sizeof(flexis_support_result) * (size_t)nP));
+    if (nSel > 0) CK(alloc((void **)&w.sel_buf, sizeof(int32_t) * (size_t)nSel * MAXN));
     CK(cudaMallocHost((void **)&w.h_ctl, sizeof(Ctl)));
     w.P = nP;
-    w.W = nW;
-    w.sel = nS;
+    w.slots = nSlots;
+    w.sel_slots = nSel;
+    w.bytes = b;
     return FLEXIS_OK;
 }
 
@@ -992,6 +1022,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
         stats->alg_bytes_greedy = (int64_t)w.h_ctl->bytes_greedy;
         stats->alg_bytes = (int64_t)(w.h_ctl->bytes_greedy + w.h_ctl->bytes_mni);
         stats->search_launches = search_launches;
+        stats->d2h_bytes = (int64_t)sizeof(Ctl) * (rounds / R + 1);  // control-word reads
         float t = 0.f;
         cudaEventElapsedTime(&t, g->ev[0], g->ev[1]);
         stats->total_ms = t;
@@ -1026,6 +1057,10 @@ int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support
     CK(cudaMemcpyAsync(h_results, w.results, sizeof(flexis_support_result) * (size_t)P,
                        cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    if (stats) {
+        stats->h2d_bytes += (int64_t)sizeof(Plan) * P;
+        stats->d2h_bytes += (int64_t)sizeof(flexis_support_result) * P;
+    }
     return FLEXIS_OK;
 }
 

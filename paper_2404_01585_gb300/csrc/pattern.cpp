@@ -260,7 +260,13 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
         }
         p.lab[i] = r;
     }
-    Code code = canonical(p, nullptr);
+    fill_plan(g, canonical(p, nullptr), P);
+    return FLEXIS_OK;
+}
+
+// Matching orders, label slices and (when MNI is wanted) orbit plans of a canonical pattern
+// whose labels are ranks of g.
+void fill_plan(const HostGraph &g, const Code &code, Plan &P) {
     Pat q = pat_of_code(code);
     P.code_n = code.n;
     for (int i = 0; i < code.n; i++) P.code_lab[i] = (uint8_t)code.lab[i];
@@ -275,6 +281,8 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
     P.greedy = level_plan(q, 0);
     P.root_begin = P.lab_begin[0];
     P.root_end = P.lab_end[0];
+    P.n_orb = 0;
+    if (!P.want_mni) return;
     int orb[MAXN];
     orbits(q, orb);
     int k = 0;
@@ -284,6 +292,24 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
         k++;
     }
     P.n_orb = k;
+}
+
+// Plan of a pattern already in canonical form over the graph's label ranks (mining candidates).
+int compile_code(const HostGraph &g, const Code &code, int64_t sigma, int64_t lam_num,
+                 int64_t lam_den, int mode, Plan &P) {
+    memset(&P, 0, sizeof P);
+    P.n = code.n;
+    P.sigma = sigma;
+    P.want_mni = (mode & FLEXIS_MODE_NO_MNI) ? 0 : 1;
+    mode &= ~FLEXIS_MODE_NO_MNI;
+    P.mode = mode;
+    if (!P.want_mni) P.flags |= FLEXIS_FLAG_MNI_SKIPPED;
+    P.n_edges = edge_count(pat_of_code(code));
+    P.tau = tau_exact(sigma, lam_num, lam_den, code.n);
+    const int64_t c = P.tau > 1 ? P.tau : 1;
+    P.cap = mode == FLEXIS_MODE_EARLY ? c : CAP_INF;
+    P.status = FLEXIS_OK;
+    fill_plan(g, code, P);
     return FLEXIS_OK;
 }
 
