@@ -82,7 +82,9 @@ typedef struct {
     int32_t window_max;   /* 0 = autotuned */
     int32_t search_blocks;/* blocks of the search kernel: 0 = autotuned (multiple of the SM count) */
     int32_t record_selected; /* >0: keep up to this many selected maps per pattern (tests) */
-    int32_t reserved[9];
+    int32_t search_budget;   /* candidate chunks a root search runs per round before it is
+                                suspended and resumed in the next round: 0 = default, -1 = never */
+    int32_t reserved[8];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

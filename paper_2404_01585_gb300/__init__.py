@@ -45,7 +45,8 @@ class FlexisError(RuntimeError):
 class flexis_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("device", C.c_int32), ("window_min", C.c_int32),
                 ("window_max", C.c_int32), ("search_blocks", C.c_int32),
-                ("record_selected", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("record_selected", C.c_int32), ("search_budget", C.c_int32),
+                ("reserved", C.c_int32 * 8)]
 
 
 class flexis_pattern(C.Structure):

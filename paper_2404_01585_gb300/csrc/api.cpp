@@ -93,6 +93,7 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.record_selected = g->opt.record_selected;
     c.rounds_per_sync = P >= 64 ? 4 : 2;
     c.timing = g->opt.reserved[0] != 0;
+    c.search_budget = g->opt.search_budget;
     return c;
 }
 

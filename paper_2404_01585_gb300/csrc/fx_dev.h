@@ -14,6 +14,7 @@ struct EvalConfig {
     int32_t search_blocks = 0;  // 0: SM count x resident blocks per SM
     int32_t record_selected = 0;
     int32_t rounds_per_sync = 4;
+    int32_t search_budget = 0;  // 0: default per-round budget; < 0: unlimited
     bool timing = false;        // per-launch CUDA events around the search kernel
 };
 

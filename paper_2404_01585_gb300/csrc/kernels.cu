@@ -41,7 +41,9 @@ namespace fx {
 
 #define FULLMASK 0xFFFFFFFFu
 
-enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2 };
+// window slot states; a SUSPENDED slot's search ran out of its per-round budget (its saved
+// state index is in the slot's first map entry)
+enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SUSPENDED = 3 };
 
 struct DevGraphView {
     const VRec *vrec;
@@ -70,6 +72,8 @@ struct PatState {
     unsigned long long steps;  // candidate chunks scanned by the greedy searches
     uint32_t max_steps;        // largest chunk count of one greedy search
     int32_t buf;               // current window buffer (0 or 1)
+    uint32_t susp_mask;        // saved-search slots in use (KSUSP bits)
+    uint32_t pad3;
 };
 
 struct Ctl {
@@ -93,6 +97,7 @@ struct Batch {
     int32_t Wmax;
     int32_t Wmin;
     int32_t sel_cap;
+    uint32_t budget;      // per-round candidate chunks of one root search (0: unlimited)
     PatState *st;
     uint32_t *used;       // [P][words]
     int32_t *win_root;    // [P][2][Wmax]  two window buffers per pattern
@@ -102,6 +107,7 @@ struct Batch {
     Ctl *ctl;
     int32_t *sel;         // [P][sel_cap][8] selected maps, canonical vertex order
     unsigned long long *mni_seg;  // [P*8+1] prefix sums of MNI candidate segments
+    uint32_t *susp;               // [P][KSUSP][DFS_SAVE_STRIDE] saved search states
     flexis_support_result *results;
 };
 
@@ -113,11 +119,19 @@ struct WarpState {
     uint32_t conf[MAXN];                // backjump conflict set of each level (bits of levels)
     uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
     int32_t nchk[MAXN];
+    int32_t level;                      // level at suspension
+    int32_t pad0;
+    // --- the fields above are the resumable search state (DFS_SAVE_WORDS words)
     unsigned long long need[MAXN];      // neighbour labels each canonical vertex needs
     LevelPlan L;
     int32_t n;
     int32_t pad[1];
 };
+constexpr int DFS_SAVE_WORDS = (int)(offsetof(WarpState, need) / 4);
+constexpr int DFS_SAVE_STRIDE = 192;  // words per saved state (>= DFS_SAVE_WORDS)
+static_assert(DFS_SAVE_WORDS <= DFS_SAVE_STRIDE, "saved search state too large");
+constexpr int KSUSP = 8;              // suspended searches a pattern may hold at once
+constexpr uint32_t SEARCH_BUDGET = 2048;  // candidate chunks a root search runs per round
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
@@ -243,28 +257,49 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // candidate by injectivity, and the conflict levels handed up by deeper failures.  Levels in
 // between cannot make level i succeed, so skipping their remaining candidates removes only
 // subtrees without a map: the first map found in lexicographic order is unchanged.
-__device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
-                          unsigned long long &bytes, uint32_t &probes, uint32_t &steps) {
+//
+// Resumable: with budget > 0 the search stops after `budget` candidate chunks and returns
+// DFS_SUSPENDED with its whole state in W (current level in W.level).  It may later continue
+// (resume = true) under a larger used set: bound vertices that have become used are dropped
+// (the search continues at the first such level with that level's remaining candidates) and
+// every popped candidate is re-tested against the used set.  Everything skipped before the
+// suspension failed under the smaller used set and fails under the larger one, so the first map
+// found is the first map avoiding the current used set.
+enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2 };
+
+__device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
+                       unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
+                       bool resume) {
     const int lane = threadIdx.x & 31;
     const int n = W.n;
-    if (lane == 0) W.t[0] = root;
-    __syncwarp();
-    if (used) {
-        bytes += 4;
-        if (used_bit(used, root)) return false;
-    }
-    bytes += 32;
-    if (!vertex_fits(G, root, W.L.deg[0], W.need[W.L.vert[0]])) return false;
     int i = 1;
-    bool ok = enter_level(G, W, 1, bytes);
+    bool ok;
     uint32_t hi = 0, pos = 0, base = 0, mask = 0, conf = 0;
-    if (ok) { hi = W.hi[1]; pos = W.lo[1]; }
+    if (!resume) {
+        if (lane == 0) W.t[0] = root;
+        __syncwarp();
+        if (used) {
+            bytes += 4;
+            if (used_bit(used, root)) return DFS_NONE;
+        }
+        bytes += 32;
+        if (!vertex_fits(G, root, W.L.deg[0], W.need[W.L.vert[0]])) return DFS_NONE;
+        ok = enter_level(G, W, 1, bytes);
+        if (ok) { hi = W.hi[1]; pos = W.lo[1]; }
+    } else {
+        if (used && used_bit(used, W.t[0])) return DFS_NONE;
+        i = W.level;
+        for (int l = 1; l < i; l++)
+            if (used && used_bit(used, W.t[l])) { i = l; break; }
+        hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i]; conf = W.conf[i];
+        ok = true;
+    }
     for (;;) {
         if (!ok) {
             // level i has no candidate left: jump to the deepest level of its conflict set
             const uint32_t cs = (conf | W.L.bmask[i]) & ((1u << i) - 1u);
             const int h = 31 - __clz(cs);
-            if (h <= 0) return false;  // only the root is to blame: this root has no map
+            if (h <= 0) return DFS_NONE;  // only the root is to blame: this root has no map
             conf = W.conf[h] | (cs & ~(1u << h));
             i = h;
             hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i];
@@ -273,6 +308,14 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
         }
         if (mask == 0) {
             if (pos >= hi) { ok = false; continue; }
+            if (budget && steps >= budget) {
+                if (lane == 0) {
+                    W.level = i;
+                    W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = 0; W.conf[i] = conf;
+                }
+                __syncwarp();
+                return DFS_SUSPENDED;
+            }
             const uint32_t k = pos + lane;
             bool good = false;
             uint32_t rej = 0;
@@ -288,8 +331,9 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
         const int j = __ffs(mask) - 1;
         mask &= mask - 1;
         const int32_t c = __ldg(G.adj + base + j);
+        if (resume && used && used_bit(used, c)) continue;  // became used since the chunk scan
         if (lane == 0) W.t[i] = c;
-        if (i == n - 1) { __syncwarp(); return true; }
+        if (i == n - 1) { __syncwarp(); return DFS_FOUND; }
         if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
         __syncwarp();
         ++i;
@@ -297,6 +341,12 @@ __device__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *u
         ok = enter_level(G, W, i, bytes);
         if (ok) { hi = W.hi[i]; pos = W.lo[i]; mask = 0; }
     }
+}
+
+__device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
+                                          int32_t root, unsigned long long &bytes, uint32_t &probes,
+                                          uint32_t &steps) {
+    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
 }
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {
@@ -360,7 +410,7 @@ __global__ void k_admit(Batch B, const int32_t *slots, int n) {
 __global__ void k_reset_ctl(Batch B) { reset_ctl(B.ctl); }
 
 // One warp per (pattern, slot) item: first map of the slot's root avoiding the used set.
-__global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch B, int q) {
+__global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     __shared__ WarpState ws[SEARCH_THREADS / 32];
     const int lane = threadIdx.x & 31;
     WarpState &W = ws[threadIdx.x >> 5];
@@ -378,14 +428,49 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch B, int q) {
         load_level_plan(W, P.greedy, P);
         const size_t slot = (size_t)p * 2 * B.Wmax + s;  // s includes the buffer offset
         const int32_t root = B.win_root[slot];
+        const uint32_t *used = B.used + (size_t)p * B.G.words;
+        const bool resume = B.win_state[slot] == SLOT_SUSPENDED;
+        int sid = -1;
+        if (resume) {  // continue a search suspended in an earlier round
+            sid = B.win_map[slot * MAXN];
+            const uint32_t *src = B.susp + ((size_t)p * KSUSP + sid) * DFS_SAVE_STRIDE;
+            for (int w = lane; w < DFS_SAVE_WORDS; w += 32) reinterpret_cast<uint32_t *>(&W)[w] = src[w];
+            __syncwarp();
+        }
         uint32_t steps = 0;
-        const bool found = dfs_first(B.G, W, B.used + (size_t)p * B.G.words, root, bytes, probes, steps);
+        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
+        if (r == DFS_SUSPENDED && sid < 0) {
+            int got = -1;
+            if (lane == 0) {  // claim a free saved-state slot of this pattern
+                unsigned int *m = &B.st[p].susp_mask;
+                unsigned int cur = atomicAdd(m, 0u);
+                for (int tries = 0; tries < 64 && got < 0; tries++) {
+                    const unsigned int freeb = ~cur & ((1u << KSUSP) - 1u);
+                    if (!freeb) break;
+                    const int b = __ffs(freeb) - 1;
+                    const unsigned int prev = atomicCAS(m, cur, cur | (1u << b));
+                    if (prev == cur) got = b; else cur = prev;
+                }
+            }
+            sid = __shfl_sync(FULLMASK, got, 0);
+            if (sid < 0) r = dfs_run(B.G, W, used, root, bytes, probes, steps, 0, true);  // no room
+        }
         if (lane == 0 && steps) {
             atomicAdd(&B.st[p].steps, (unsigned long long)steps);
             atomicMax(&B.st[p].max_steps, steps);
         }
-        if (lane == 0) B.win_state[slot] = found ? SLOT_MAP : SLOT_NONE;
-        if (found && lane < P.n) B.win_map[slot * MAXN + lane] = W.t[lane];
+        if (r == DFS_SUSPENDED) {
+            uint32_t *dst = B.susp + ((size_t)p * KSUSP + sid) * DFS_SAVE_STRIDE;
+            for (int w = lane; w < DFS_SAVE_WORDS; w += 32) dst[w] = reinterpret_cast<const uint32_t *>(&W)[w];
+            if (lane == 0) {
+                B.win_state[slot] = SLOT_SUSPENDED;
+                B.win_map[slot * MAXN] = sid;
+            }
+        } else {
+            if (sid >= 0 && lane == 0) atomicAnd(&B.st[p].susp_mask, ~(1u << sid));
+            if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
+            if (r == DFS_FOUND && lane < P.n) B.win_map[slot * MAXN + lane] = W.t[lane];
+        }
         __syncwarp();
     }
     unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
@@ -505,6 +590,9 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         if (st_cur[s] != SLOT_MAP) continue;
         if (owner(mp_cur[(size_t)s * MAXN + k]) < s) atomicMin(&s_f, s);
     }
+    // a suspended search is undecided: nothing at or after it can be committed yet
+    for (int s = tid; s < horizon; s += nthr)
+        if (st_cur[s] == SLOT_SUSPENDED) atomicMin(&s_f, s);
     __syncthreads();
     const int f = s_f;
     // 4. commit the map slots before f, in slot order
@@ -544,6 +632,8 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
                     mp_nxt[(size_t)r * MAXN + l] = m[l];
                     if (owner(m[l]) < f) state = SLOT_NEEDS;
                 }
+            } else if (state == SLOT_SUSPENDED) {
+                mp_nxt[(size_t)r * MAXN] = mp_cur[(size_t)s * MAXN];  // saved-state index
             }
             rt_nxt[r] = rt_cur[s];
             st_nxt[r] = state;
@@ -587,14 +677,15 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     for (int b0 = 0; b0 < nw; b0 += nthr) {
         const int s = b0 + tid;
         int excl;
-        nitems += block_scan((s < nw && st_nxt[s] == SLOT_NEEDS) ? 1 : 0, excl, sh_scan);
+        nitems += block_scan((s < nw && (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_SUSPENDED)) ? 1 : 0,
+                             excl, sh_scan);
     }
     if (tid == 0) s_base = nitems ? atomicAdd(&B.ctl->n_items[q], nitems) : 0;
     __syncthreads();
     int wr = s_base;
     for (int b0 = 0; b0 < nw; b0 += nthr) {
         const int s = b0 + tid;
-        const int nd = (s < nw && st_nxt[s] == SLOT_NEEDS) ? 1 : 0;
+        const int nd = (s < nw && (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_SUSPENDED)) ? 1 : 0;
         int excl;
         const int tot = block_scan(nd, excl, sh_scan);
         if (nd) B.items[wr + excl] = make_int2(p, nxt * Wmax + s);
@@ -777,6 +868,7 @@ struct Workspace {
     Ctl *ctl = nullptr;
     int32_t *sel_buf = nullptr;
     unsigned long long *mni_seg = nullptr;
+    uint32_t *susp = nullptr;
     Plan *plans = nullptr;                   // device plan array (host-plan entry points)
     flexis_support_result *results = nullptr;
     int32_t plans_cap = 0;
@@ -810,7 +902,7 @@ static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
 int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes) {
     *bytes = (int64_t)g->view.words * 4 + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) +
              (int64_t)sizeof(PatState) + (int64_t)sizeof(Plan) + (int64_t)sizeof(flexis_support_result) +
-             8 * (MAXN + 1) + (int64_t)sel * 4 * MAXN;
+             8 * (MAXN + 1) + (int64_t)sel * 4 * MAXN + 4ll * KSUSP * DFS_SAVE_STRIDE;
     return FLEXIS_OK;
 }
 
@@ -856,7 +948,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
 static void ws_free(Workspace &w) {
     cudaFree(w.st); cudaFree(w.used); cudaFree(w.win_root); cudaFree(w.win_state);
     cudaFree(w.win_map); cudaFree(w.items); cudaFree(w.ctl); cudaFree(w.sel_buf);
-    cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results);
+    cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results); cudaFree(w.susp);
     if (w.h_ctl) cudaFreeHost(w.h_ctl);
     w = Workspace();
 }
@@ -886,6 +978,7 @@ static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax
     CK(alloc((void **)&w.items, sizeof(int2) * (size_t)nSlots));
     CK(alloc((void **)&w.ctl, sizeof(Ctl)));
     CK(alloc((void **)&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
+    CK(alloc((void **)&w.susp, sizeof(uint32_t) * (size_t)nP * KSUSP * DFS_SAVE_STRIDE));
     CK(alloc((void **)&w.plans, sizeof(Plan) * (size_t)nP));
     CK(alloc((void **)&w.results, sizeof(flexis_support_result) * (size_t)nP));
     if (nSel > 0) CK(alloc((void **)&w.sel_buf, sizeof(int32_t) * (size_t)nSel * MAXN));
@@ -928,6 +1021,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
     B.Wmax = Wmax;
     B.Wmin = Wmin;
     B.sel_cap = sel;
+    B.budget = SEARCH_BUDGET;
     B.st = w.st;
     B.used = w.used;
     B.win_root = w.win_root;
@@ -937,6 +1031,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
     B.ctl = w.ctl;
     B.sel = sel > 0 ? w.sel_buf : nullptr;
     B.mni_seg = w.mni_seg;
+    B.susp = w.susp;
     B.results = results;
     return B;
 }
@@ -960,6 +1055,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     g->last_P = P;
     g->last_sel = cfg.record_selected;
     Batch B = make_batch(g, w, d_plans, P, Wmin, Wmax, cfg.record_selected, d_results);
+    if (cfg.search_budget != 0) B.budget = cfg.search_budget < 0 ? 0u : (uint32_t)cfg.search_budget;
     const size_t smem = commit_smem(Wmax);
     const int sblocks = search_grid(g, cfg);
 

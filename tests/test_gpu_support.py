@@ -117,9 +117,10 @@ def test_large_patterns_vs_oracle(er_large_patterns, mode):
 
 
 @pytest.mark.parametrize("mode", [EARLY, FULL])
-def test_powerlaw_batch_vs_oracle(powerlaw, mode):
+@pytest.mark.parametrize("budget", [0, 2])
+def test_powerlaw_batch_vs_oracle(powerlaw, mode, budget):
     lab, src, dst, pats = powerlaw
-    g = fx.Graph(lab, src, dst)
+    g = fx.Graph(lab, src, dst, search_budget=budget)
     og = oracle.Graph(lab, src, dst)
     for sigma, lam in ((60, 0.5), (400, 1.0), (5, 0.0)):
         check_batch(g, og, pats, sigma, lam, mode)
@@ -130,7 +131,9 @@ def test_plain_equals_batched_and_launch_shape_free(powerlaw):
     lab, src, dst, pats = powerlaw
     ref = None
     for opts in ({}, dict(window_min=1, window_max=32), dict(window_min=1024, window_max=1024),
-                 dict(search_blocks=3), dict(window_min=7, window_max=64, search_blocks=151)):
+                 dict(search_blocks=3), dict(window_min=7, window_max=64, search_blocks=151),
+                 dict(search_budget=1), dict(search_budget=3, window_min=4096, window_max=16384),
+                 dict(search_budget=-1)):
         g = fx.Graph(lab, src, dst, **opts)
         for mode in (EARLY, FULL):
             batch = [key(r) for r in g.support_batch(pats, 60, 0.5, mode)]
@@ -144,9 +147,12 @@ def test_plain_equals_batched_and_launch_shape_free(powerlaw):
         g.close()
 
 
-def test_selected_maps_equal_oracle(powerlaw):
+@pytest.mark.parametrize("budget", [0, 1])
+def test_selected_maps_equal_oracle(powerlaw, budget):
+    # budget 1: every root search is suspended after each candidate chunk and resumed in the next
+    # round under a grown used set
     lab, src, dst, pats = powerlaw
-    g = fx.Graph(lab, src, dst, record_selected=4096)
+    g = fx.Graph(lab, src, dst, record_selected=4096, search_budget=budget)
     og = oracle.Graph(lab, src, dst)
     res = g.support_batch(pats[:30], 60, 0.5, FULL)
     for i, ((pl, pe), r) in enumerate(zip(pats[:30], res)):
@@ -201,9 +207,10 @@ def test_mine_citeseer_shape():
     g.close()
 
 
-def test_mine_small_powerlaw(powerlaw):
+@pytest.mark.parametrize("budget", [0, 1])
+def test_mine_small_powerlaw(powerlaw, budget):
     lab, src, dst, _ = powerlaw
-    g = fx.Graph(lab, src, dst)
+    g = fx.Graph(lab, src, dst, search_budget=budget)
     og = oracle.Graph(lab, src, dst)
     got, glev = g.mine(300, 0.5, 3)
     want, wlev = og.mine(sigma=300, lam=0.5, max_edges=3)
@@ -232,4 +239,16 @@ def test_serving_alone_equals_mixed(powerlaw):
         time.sleep(0.001)
     srv.stop()
     assert [key(got[i]) for i in range(len(pats))] == alone
+    g.close()
+
+
+def test_no_mni_mode(powerlaw):
+    lab, src, dst, pats = powerlaw
+    g = fx.Graph(lab, src, dst)
+    og = oracle.Graph(lab, src, dst)
+    res = g.support_batch(pats, 60, 0.5, EARLY | fx.FLEXIS_MODE_NO_MNI)
+    for (pl, pe), r in zip(pats, res):
+        w = og.support(pl, pe, sigma=60, lam=0.5, mode="early", tier=1)
+        assert (r["tau"], r["mis"], bool(r["frequent"])) == (w["tau"], w["mis"], w["frequent"])
+        assert r["mni"] == -1 and r["flags"] & fx.FLEXIS_FLAG_MNI_SKIPPED
     g.close()
