@@ -208,9 +208,9 @@ def main():
         cand, freq = 0, 0
         acc = {}
         for sigma, lam in SWEEP:
-            pats, levels = g.mine(sigma, lam, MAX_EDGES)
+            arr, levels = g.mine_arrays(sigma, lam, MAX_EDGES)
             cand += sum(c for c, _ in levels.values())
-            freq += len(pats)
+            freq += int(arr["n"].size)
             st = g.stats()
             for k, v in st.items():
                 acc[k] = acc.get(k, 0) + v
@@ -278,11 +278,11 @@ def main():
         g2 = fx.Graph(lab, src, dst, device=local)
         info = g2.info()
         for sigma, lam in SWEEP:
-            pats, levels = g2.mine(sigma, lam, MAX_EDGES)
+            arr, levels = g2.mine_arrays(sigma, lam, MAX_EDGES)
             e2e_c += sum(c for c, _ in levels.values())
             st = g2.stats()
             h2d += st["h2d_bytes"]
-            d2h += st["d2h_bytes"] + 80 * len(pats)
+            d2h += st["d2h_bytes"] + 80 * int(arr["n"].size)
         h2d += info["device_bytes"]
         g2.close()
         torch.cuda.synchronize()

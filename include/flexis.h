@@ -228,6 +228,12 @@ int64_t flexis_pattern_set_count(const flexis_pattern_set *s);
 int flexis_pattern_set_get(const flexis_pattern_set *s, int64_t i, int32_t *n, int32_t *labels,
                            int32_t *m, int32_t *edges, int32_t *code_labels, uint32_t *code_bits,
                            flexis_support_result *result);
+/* Patterns first .. first+count-1 in one call: n_out[count], code_labels[count*8] (label ranks in
+ * canonical order), code_bits[count], labels_out[count*8] (label ids, nullable),
+ * results[count] (nullable).  Returns the number written (fewer at the end of the set).       */
+int64_t flexis_pattern_set_read(const flexis_pattern_set *s, int64_t first, int64_t count,
+                                int32_t *n_out, int32_t *code_labels, uint32_t *code_bits,
+                                int32_t *labels_out, flexis_support_result *results);
 /* per level k (0..8): candidates evaluated and frequent patterns found */
 int flexis_pattern_set_levels(const flexis_pattern_set *s, int64_t *candidates, int64_t *frequent);
 void flexis_free_pattern_set(flexis_pattern_set *s);

@@ -117,6 +117,9 @@ SYMBOLS = {
     "flexis_pattern_set_get": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P, _I32P, _I32P,
                                           C.POINTER(C.c_uint32), C.POINTER(flexis_support_result)]),
     "flexis_pattern_set_levels": (C.c_int, [_P, _I64P, _I64P]),
+    "flexis_pattern_set_read": (C.c_int64, [_P, C.c_int64, C.c_int64, _I32P, _I32P,
+                                            C.POINTER(C.c_uint32), _I32P,
+                                            C.POINTER(flexis_support_result)]),
     "flexis_free_pattern_set": (None, [_P]),
     "flexis_canonical_code": (C.c_int, [C.POINTER(flexis_pattern), _I32P, C.POINTER(C.c_uint32), _I32P]),
     "flexis_generate_candidates": (C.c_int64, [C.POINTER(flexis_pattern), C.c_int32, C.c_int32, _I32P,
@@ -294,33 +297,55 @@ class Graph:
         """Algorithm 1.  Returns (patterns, levels): patterns = list of dict(n, labels, edges,
         code_labels, code_bits, tau, mis, mni) sorted by (n, canonical code); levels maps
         k -> (candidates, frequent)."""
+        arr, levels = self.mine_arrays(sigma, lam, max_edges)
+        out = []
+        for i in range(arr["n"].size):
+            n = int(arr["n"][i])
+            bits = int(arr["code_bits"][i])
+            # edges of the canonical pattern from its code bits (column j, rows i < j; bit set =
+            # not adjacent; first bit most significant)
+            edges, t = [], n * (n - 1) // 2 - 1
+            for b in range(1, n):
+                for a in range(b):
+                    if not (bits >> t) & 1:
+                        edges.append((a, b))
+                    t -= 1
+            out.append(dict(n=n, labels=tuple(int(x) for x in arr["labels"][i, :n]), edges=edges,
+                            code_labels=tuple(int(x) for x in arr["code_labels"][i, :n]), code_bits=bits,
+                            tau=int(arr["tau"][i]), mis=int(arr["mis"][i]), mni=int(arr["mni"][i]),
+                            frequent=True))
+        return out, levels
+
+    def mine_arrays(self, sigma, lam, max_edges):
+        """Algorithm 1 with the frequent set read back in one call: (dict of numpy arrays n,
+        code_labels, code_bits, labels, tau, mis, mni; levels)."""
         L = lib()
         h = _P()
         _check(L.flexis_mine(self._h, sigma, float(lam), max_edges, C.byref(h)), "flexis_mine")
         try:
-            cnt = L.flexis_pattern_set_count(h)
-            out = []
-            n = C.c_int32()
-            m = C.c_int32()
-            lab = np.zeros(8, np.int32)
-            clab = np.zeros(8, np.int32)
-            edg = np.zeros(56, np.int32)
-            bits = C.c_uint32()
-            r = flexis_support_result()
-            for i in range(cnt):
-                _check(L.flexis_pattern_set_get(h, i, C.byref(n), lab.ctypes.data_as(_I32P), C.byref(m),
-                                                edg.ctypes.data_as(_I32P), clab.ctypes.data_as(_I32P),
-                                                C.byref(bits), C.byref(r)), "flexis_pattern_set_get")
-                d = r.as_dict()
-                d.update(n=n.value, labels=tuple(int(x) for x in lab[: n.value]),
-                         edges=[(int(edg[2 * j]), int(edg[2 * j + 1])) for j in range(m.value)],
-                         code_labels=tuple(int(x) for x in clab[: n.value]), code_bits=int(bits.value))
-                out.append(d)
+            cnt = int(L.flexis_pattern_set_count(h))
+            n = np.zeros(max(cnt, 1), np.int32)
+            clab = np.zeros((max(cnt, 1), 8), np.int32)
+            lab = np.zeros((max(cnt, 1), 8), np.int32)
+            bits = np.zeros(max(cnt, 1), np.uint32)
+            res = (flexis_support_result * max(cnt, 1))()
+            got = L.flexis_pattern_set_read(h, 0, cnt, n.ctypes.data_as(_I32P), clab.ctypes.data_as(_I32P),
+                                            bits.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                            lab.ctypes.data_as(_I32P), res)
+            if got != cnt:
+                raise FlexisError(FLEXIS_E_INVALID, "flexis_pattern_set_read")
+            rr = np.frombuffer(res, dtype=np.dtype([("status", "<i4"), ("n", "<i4"), ("sigma", "<i8"),
+                                                   ("tau", "<i8"), ("cap", "<i8"), ("mis", "<i8"),
+                                                   ("mni", "<i8"), ("frequent", "<i4"), ("flags", "<u4"),
+                                                   ("roots", "<i8"), ("steps", "<i8"), ("maxsteps", "<i4"),
+                                                   ("rounds", "<i4")]), count=cnt)
             cand = np.zeros(9, np.int64)
             freq = np.zeros(9, np.int64)
             L.flexis_pattern_set_levels(h, cand.ctypes.data_as(_I64P), freq.ctypes.data_as(_I64P))
             levels = {k: (int(cand[k]), int(freq[k])) for k in range(2, 9) if cand[k] > 0}
-            return out, levels
+            arr = dict(n=n[:cnt], code_labels=clab[:cnt], code_bits=bits[:cnt], labels=lab[:cnt],
+                       tau=rr["tau"].copy(), mis=rr["mis"].copy(), mni=rr["mni"].copy())
+            return arr, levels
         finally:
             L.flexis_free_pattern_set(h)
 

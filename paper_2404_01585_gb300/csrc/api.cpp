@@ -365,6 +365,27 @@ int flexis_pattern_set_get(const flexis_pattern_set *s, int64_t i, int32_t *n, i
     return FLEXIS_OK;
 }
 
+int64_t flexis_pattern_set_read(const flexis_pattern_set *s, int64_t first, int64_t count,
+                                int32_t *n_out, int32_t *code_labels, uint32_t *code_bits,
+                                int32_t *labels_out, flexis_support_result *results) {
+    if (!s || first < 0 || count < 0 || (count > 0 && (!n_out || !code_labels || !code_bits)))
+        return FLEXIS_E_INVALID;
+    const int64_t end = std::min<int64_t>((int64_t)s->items.size(), first + count);
+    for (int64_t i = first; i < end; i++) {
+        const auto &e = s->items[(size_t)i];
+        const int64_t k = i - first;
+        n_out[k] = e.code.n;
+        for (int j = 0; j < MAXN; j++) {
+            const int32_t r = j < e.code.n ? e.code.lab[j] : 0;
+            code_labels[8 * k + j] = r;
+            if (labels_out) labels_out[8 * k + j] = j < e.code.n ? s->label_of_rank[(size_t)r] : -1;
+        }
+        code_bits[k] = e.code.bits;
+        if (results) results[k] = e.res;
+    }
+    return std::max<int64_t>(0, end - first);
+}
+
 int flexis_pattern_set_levels(const flexis_pattern_set *s, int64_t *candidates, int64_t *frequent) {
     if (!s) return FLEXIS_E_INVALID;
     for (int k = 0; k <= FLEXIS_MAX_PATTERN; k++) {

@@ -131,7 +131,7 @@ constexpr int DFS_SAVE_WORDS = (int)(offsetof(WarpState, need) / 4);
 constexpr int DFS_SAVE_STRIDE = 192;  // words per saved state (>= DFS_SAVE_WORDS)
 static_assert(DFS_SAVE_WORDS <= DFS_SAVE_STRIDE, "saved search state too large");
 constexpr int KSUSP = 8;              // suspended searches a pattern may hold at once
-constexpr uint32_t SEARCH_BUDGET = 2048;  // candidate chunks a root search runs per round
+constexpr uint32_t SEARCH_BUDGET = 512;  // candidate chunks a root search runs per round
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
