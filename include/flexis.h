@@ -203,6 +203,29 @@ int flexis_compile(flexis_graph *g, const flexis_pattern *patterns, const int64_
 int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int32_t count,
                                 flexis_support_result *d_results, void *stream);
 
+/* Support of one compiled pattern without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc during evaluation -- code that
+ * runs under a device-memory budget owned by another framework (whose allocator it must not
+ * bypass), or on a latency-critical path where cudaMalloc/cudaFree would implicitly synchronise
+ * the device.  All device scratch (control words, pattern state, window buffers, work items,
+ * saved searches, used-vertex bitmap) comes from one static device array of 8 MiB that every GPU
+ * loading this library holds until the process exits; the call allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library routine).
+ *   plan   : host pointer to one plan from flexis_compile (the caller passes the input)
+ *   out    : host pointer, receives the result (same values as flexis_support on that pattern)
+ *   stream : cudaStream_t to run on, NULL = the graph's stream; the call synchronises it
+ * Limits: one pattern per call, speculation window of 1024 roots, and the used-vertex bitmap
+ * (n_vertices / 8 bytes) must fit the array beside about 96 KiB of other scratch, i.e. graphs of
+ * up to about 66 million vertices; larger graphs return FLEXIS_E_UNSUPPORTED with the exact limit
+ * printed on stderr.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device); make that first call before any stream capture.  Every call on a device shares the
+ * array and it keeps the last call's contents (the call clears what must start at zero): calls
+ * whose work overlaps on the GPU -- on different streams or from different threads -- race, so
+ * serialise them.                                                                               */
+int flexis_support_noalloc(flexis_graph *g, const flexis_plan *plan, flexis_support_result *out,
+                           void *stream);
+
 /* Counters of the last evaluation call on g. */
 int flexis_last_stats(const flexis_graph *g, flexis_stats *out);
 

@@ -111,6 +111,7 @@ SYMBOLS = {
     "flexis_support_plans_device": (C.c_int, [_P, _P, C.c_int32, _P, _P]),
     "flexis_last_stats": (C.c_int, [_P, C.POINTER(flexis_stats)]),
     "flexis_graph_stream": (C.c_void_p, [_P]),
+    "flexis_support_noalloc": (C.c_int, [_P, C.POINTER(flexis_plan), C.POINTER(flexis_support_result), _P]),
     "flexis_selected_maps": (C.c_int, [_P, C.c_int32, _I32P, C.c_int64, _I64P]),
     "flexis_mine": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int32, C.POINTER(_P)]),
     "flexis_pattern_set_count": (C.c_int64, [_P]),
@@ -276,6 +277,16 @@ class Graph:
         rc = lib().flexis_support_plans_device(self._h, C.c_void_p(d_plans_ptr), count,
                                                C.c_void_p(d_results_ptr), C.c_void_p(stream_ptr))
         _check(rc, "flexis_support_plans_device")
+
+    def support_noalloc(self, plan: np.ndarray, stream: int = 0) -> dict:
+        """flexis_support_noalloc on one compiled plan (a uint8[1024] row of compile())."""
+        buf = np.ascontiguousarray(plan, dtype=np.uint8).reshape(-1)
+        if buf.size != C.sizeof(flexis_plan):
+            raise ValueError("one plan of %d bytes expected" % C.sizeof(flexis_plan))
+        r = flexis_support_result()
+        _check(lib().flexis_support_noalloc(self._h, buf.ctypes.data_as(C.POINTER(flexis_plan)),
+                                            C.byref(r), C.c_void_p(stream)), "flexis_support_noalloc")
+        return r.as_dict()
 
     def stream(self) -> int:
         """cudaStream_t (as an int) on which this graph's evaluations run."""

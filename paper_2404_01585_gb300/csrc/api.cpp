@@ -279,6 +279,12 @@ int flexis_last_stats(const flexis_graph *g, flexis_stats *out) {
 
 void *flexis_graph_stream(const flexis_graph *g) { return g ? (void *)dev_graph_stream(g->dg) : nullptr; }
 
+int flexis_support_noalloc(flexis_graph *g, const flexis_plan *plan, flexis_support_result *out,
+                           void *stream) {
+    if (!g || !plan || !out) return FLEXIS_E_INVALID;
+    return dev_support_noalloc(g->dg, reinterpret_cast<const Plan *>(plan), out, (cudaStream_t)stream);
+}
+
 int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,
                          int64_t *n_out) {
     if (!g || !maps_out || !n_out || cap < 0) return FLEXIS_E_INVALID;

@@ -40,6 +40,11 @@ int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int6
 // Device bytes one pattern of a batch holds (used bitmap, two window buffers, items, state,
 // plan, result); and the device's free memory.
 int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes);
+
+// One pattern evaluated with device scratch taken from a static device array (no allocation).
+int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_result *h_out,
+                        cudaStream_t stream);
+int64_t noalloc_max_vertices();
 int dev_free_bytes(const DeviceGraph *g, int64_t *bytes);
 
 // Serving session: `slots` pattern slots on the graph's device with their own workspace.

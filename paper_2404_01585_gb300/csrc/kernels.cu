@@ -1160,6 +1160,128 @@ int dev_eval_host(DeviceGraph *g, const Plan *h_plans, int32_t P, flexis_support
     return FLEXIS_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free evaluation
+// One pattern evaluated with all of its device scratch (control words, pattern state, plan,
+// result, window buffers, work items, saved searches, used-vertex bitmap) carved out of a single
+// statically allocated device array, so the call itself allocates nothing.  The array belongs to
+// the module: every GPU that loads the library holds it until the process exits, and every call
+// on a device reuses the same bytes.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 8ull << 20;  // 8 MiB per device
+constexpr int NOALLOC_WMAX = 1024;                    // speculation window of this entry point
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+struct NoallocLayout {
+    size_t ctl, st, plan, result, mni_seg, items, win_root, win_state, win_map, susp, used, end;
+};
+
+static NoallocLayout noalloc_layout(int64_t words) {
+    NoallocLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    L.ctl = take(sizeof(Ctl));
+    L.st = take(sizeof(PatState));
+    L.plan = take(sizeof(Plan));
+    L.result = take(sizeof(flexis_support_result));
+    L.mni_seg = take(sizeof(unsigned long long) * (MAXN + 1));
+    L.items = take(sizeof(int2) * NOALLOC_WMAX);
+    L.win_root = take(sizeof(int32_t) * 2 * NOALLOC_WMAX);
+    L.win_state = take(sizeof(int32_t) * 2 * NOALLOC_WMAX);
+    L.win_map = take(sizeof(int32_t) * 2 * NOALLOC_WMAX * MAXN);
+    L.susp = take(sizeof(uint32_t) * KSUSP * DFS_SAVE_STRIDE);
+    L.used = take(sizeof(uint32_t) * (size_t)words);
+    L.end = off;
+    return L;
+}
+
+int64_t noalloc_max_vertices() {
+    const NoallocLayout L = noalloc_layout(0);
+    return (int64_t)(NOALLOC_SCRATCH_BYTES - L.used) / 4 * 32;
+}
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_base[256];  // device address of the scratch array, per device
+
+// Set-up, once per device and with that device current: the device address of the array.  In
+// host code the array's name is only a host-side stand-in, so kernels get this address instead.
+static int noalloc_base(int device, unsigned char **out) {
+    if (device < 0 || device >= 256) return FLEXIS_E_INVALID;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            fprintf(stderr, "flexis: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+            return FLEXIS_E_CUDA;
+        }
+        g_noalloc_base[device] = (unsigned char *)p;
+    }
+    *out = g_noalloc_base[device];
+    return FLEXIS_OK;
+}
+
+int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_result *h_out,
+                        cudaStream_t stream) {
+    CK(cudaSetDevice(g->device));
+    const NoallocLayout L = noalloc_layout(g->view.words);
+    if (L.end > NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr, "flexis: flexis_support_noalloc supports graphs of at most %lld vertices "
+                        "(this graph has %lld)\n", (long long)noalloc_max_vertices(), (long long)g->view.nv);
+        return FLEXIS_E_UNSUPPORTED;
+    }
+    unsigned char *base = nullptr;
+    int rc = noalloc_base(g->device, &base);
+    if (rc) return rc;
+    if (!stream) stream = g->stream;
+    Batch B;
+    B.G = g->view;
+    B.plans = reinterpret_cast<const Plan *>(base + L.plan);
+    B.P = 1;
+    B.Wmax = NOALLOC_WMAX;
+    B.Wmin = 256;
+    B.sel_cap = 0;
+    B.budget = SEARCH_BUDGET;
+    B.st = reinterpret_cast<PatState *>(base + L.st);
+    B.used = reinterpret_cast<uint32_t *>(base + L.used);
+    B.win_root = reinterpret_cast<int32_t *>(base + L.win_root);
+    B.win_state = reinterpret_cast<int32_t *>(base + L.win_state);
+    B.win_map = reinterpret_cast<int32_t *>(base + L.win_map);
+    B.items = reinterpret_cast<int2 *>(base + L.items);
+    B.ctl = reinterpret_cast<Ctl *>(base + L.ctl);
+    B.sel = nullptr;
+    B.mni_seg = reinterpret_cast<unsigned long long *>(base + L.mni_seg);
+    B.susp = reinterpret_cast<uint32_t *>(base + L.susp);
+    B.results = reinterpret_cast<flexis_support_result *>(base + L.result);
+    // the scratch keeps the previous call's contents: the used bitmap must start empty (the
+    // pattern state and control words are rewritten by k_init)
+    CK(cudaMemcpyAsync(base + L.plan, h_plan, sizeof(Plan), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(B.used, 0, sizeof(uint32_t) * (size_t)g->view.words, stream));
+    k_init<<<1, 256, 0, stream>>>(B);
+    const int sblocks = g->sm_count * 6;
+    Ctl h_ctl;
+    for (int64_t round = 0;;) {
+        for (int r = 0; r < 2; r++, round++) {
+            const int q = (int)(round & 1);
+            k_commit<<<1, COMMIT_THREADS, commit_smem(0), stream>>>(B, q);
+            k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&h_ctl, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (h_ctl.active[(round - 1) & 1] == 0) break;
+    }
+    k_mni_setup<<<1, 1024, 0, stream>>>(B);
+    k_mni<<<sblocks, SEARCH_THREADS, 0, stream>>>(B);
+    k_finalize<<<1, 256, 0, stream>>>(B);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h_out, B.results, sizeof(flexis_support_result), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return FLEXIS_OK;
+}
+
 int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int64_t *n_out) {
     if (i < 0 || i >= g->last_P || g->last_sel <= 0 || !g->ws.sel_buf) return FLEXIS_E_INVALID;
     CK(cudaSetDevice(g->device));
