@@ -41,9 +41,14 @@ namespace fx {
 
 #define FULLMASK 0xFFFFFFFFu
 
-// window slot states; a SUSPENDED slot's search ran out of its per-round budget (its saved
-// state index is in the slot's first map entry)
-enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SUSPENDED = 3 };
+// window slot states.  A SEQ slot's root search ran out of its per-round budget: its remaining
+// search space is an ordered list of saved sub-searches (the first one's index in the slot's
+// map entry 0, each saved state holding the index of the next); the slot's map is the map of
+// the first sub-search in that order that finds one, once every earlier one has found none.
+enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3 };
+// saved sub-search status (word SUSP_STATUS of its saved state); its map in SUSP_MAP..+7
+enum : int32_t { SS_PENDING = 0, SS_NONE = 1, SS_FOUND = 2 };
+constexpr int SPLIT_MAX = 15;  // pieces one split may create
 
 struct DevGraphView {
     const VRec *vrec;
@@ -120,7 +125,7 @@ struct WarpState {
     uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
     int32_t nchk[MAXN];
     int32_t level;                      // level at suspension
-    int32_t pad0;
+    int32_t floor;                      // lowest level this search may rebind (1: whole root)
     // --- the fields above are the resumable search state (DFS_SAVE_WORDS words)
     unsigned long long need[MAXN];      // neighbour labels each canonical vertex needs
     LevelPlan L;
@@ -128,10 +133,13 @@ struct WarpState {
     int32_t pad[1];
 };
 constexpr int DFS_SAVE_WORDS = (int)(offsetof(WarpState, need) / 4);
-constexpr int DFS_SAVE_STRIDE = 192;  // words per saved state (>= DFS_SAVE_WORDS)
-static_assert(DFS_SAVE_WORDS <= DFS_SAVE_STRIDE, "saved search state too large");
-constexpr int KSUSP = 8;              // suspended searches a pattern may hold at once
-constexpr uint32_t SEARCH_BUDGET = 512;  // candidate chunks a root search runs per round
+constexpr int DFS_SAVE_STRIDE = 192;  // words per saved sub-search
+constexpr int SUSP_STATUS = DFS_SAVE_WORDS;      // SS_* of the saved sub-search
+constexpr int SUSP_NEXT = DFS_SAVE_WORDS + 1;    // next sub-search of the same slot, or -1
+constexpr int SUSP_MAP = DFS_SAVE_WORDS + 2;     // its map (by level) when SS_FOUND
+static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large");
+constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
+constexpr uint32_t SEARCH_BUDGET = 2048;  // candidate chunks a root search runs per round
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
@@ -276,7 +284,7 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
     bool ok;
     uint32_t hi = 0, pos = 0, base = 0, mask = 0, conf = 0;
     if (!resume) {
-        if (lane == 0) W.t[0] = root;
+        if (lane == 0) { W.t[0] = root; W.floor = 1; }
         __syncwarp();
         if (used) {
             bytes += 4;
@@ -290,16 +298,21 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
         if (used && used_bit(used, W.t[0])) return DFS_NONE;
         i = W.level;
         for (int l = 1; l < i; l++)
-            if (used && used_bit(used, W.t[l])) { i = l; break; }
+            if (used && used_bit(used, W.t[l])) {
+                if (l < W.floor) return DFS_NONE;  // a binding this sub-search may not change
+                i = l;
+                break;
+            }
         hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i]; conf = W.conf[i];
         ok = true;
     }
     for (;;) {
         if (!ok) {
-            // level i has no candidate left: jump to the deepest level of its conflict set
+            // level i has no candidate left: jump to the deepest level of its conflict set;
+            // below the floor the search space of this (sub-)search is exhausted
             const uint32_t cs = (conf | W.L.bmask[i]) & ((1u << i) - 1u);
             const int h = 31 - __clz(cs);
-            if (h <= 0) return DFS_NONE;  // only the root is to blame: this root has no map
+            if (h < W.floor) return DFS_NONE;
             conf = W.conf[h] | (cs & ~(1u << h));
             i = h;
             hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i];
@@ -333,7 +346,11 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
         const int32_t c = __ldg(G.adj + base + j);
         if (resume && used && used_bit(used, c)) continue;  // became used since the chunk scan
         if (lane == 0) W.t[i] = c;
-        if (i == n - 1) { __syncwarp(); return DFS_FOUND; }
+        if (i == n - 1) {  // keep the position so that a later resume continues past this map
+            if (lane == 0) { W.level = i; W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
+            __syncwarp();
+            return DFS_FOUND;
+        }
         if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
         __syncwarp();
         ++i;
@@ -409,7 +426,38 @@ __global__ void k_admit(Batch B, const int32_t *slots, int n) {
 
 __global__ void k_reset_ctl(Batch B) { reset_ctl(B.ctl); }
 
-// One warp per (pattern, slot) item: first map of the slot's root avoiding the used set.
+// Claim up to `want` free saved-sub-search indices of a pattern; returns them as a bit set.
+__device__ unsigned int claim_sids(unsigned int *m, int want) {
+    unsigned int cur = atomicAdd(m, 0u);
+    for (int tries = 0; tries < 64; tries++) {
+        constexpr unsigned int ALL = KSUSP >= 32 ? 0xFFFFFFFFu : ((1u << (KSUSP & 31)) - 1u);
+        unsigned int freeb = ~cur & ALL, take = 0;
+        for (int k = 0; k < want && freeb; k++) {
+            const unsigned int b = freeb & (~freeb + 1u);
+            take |= b;
+            freeb &= ~b;
+        }
+        if (!take) return 0;
+        const unsigned int prev = atomicCAS(m, cur, cur | take);
+        if (prev == cur) return take;
+        cur = prev;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, int status) {
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < DFS_SAVE_WORDS; w += 32) dst[w] = reinterpret_cast<const uint32_t *>(&W)[w];
+    if (lane == 0) dst[SUSP_STATUS] = status;
+    if (status == SS_FOUND && lane < MAXN) dst[SUSP_MAP + lane] = W.t[lane];
+    __syncwarp();
+}
+
+// One warp per work item.  Item (pattern, slot): a fresh search for the first map of the slot's
+// root avoiding the used set.  Item (pattern, slot, saved sub-search): continue that sub-search.
+// A search that uses up its per-round budget is saved; if it heads its slot it is also split:
+// the unscanned candidates of its shallowest level with any left go to up to five new
+// sub-searches, in order, and a continuation takes over everything after them.
 __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     __shared__ WarpState ws[SEARCH_THREADS / 32];
     const int lane = threadIdx.x & 31;
@@ -423,53 +471,119 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         it = __shfl_sync(FULLMASK, it, 0);
         if (it >= n_items) break;
         const int2 item = B.items[it];
-        const int p = item.x, s = item.y;
+        const int p = item.x;
+        const int off = item.y & 0xFFFFFF;
+        const int sid_in = (item.y >> 24) - 1;
         const Plan &P = B.plans[p];
         load_level_plan(W, P.greedy, P);
-        const size_t slot = (size_t)p * 2 * B.Wmax + s;  // s includes the buffer offset
+        const size_t slot = (size_t)p * 2 * B.Wmax + off;
+        int32_t *seq = B.win_map + slot * MAXN;
         const int32_t root = B.win_root[slot];
         const uint32_t *used = B.used + (size_t)p * B.G.words;
-        const bool resume = B.win_state[slot] == SLOT_SUSPENDED;
-        int sid = -1;
-        if (resume) {  // continue a search suspended in an earlier round
-            sid = B.win_map[slot * MAXN];
-            const uint32_t *src = B.susp + ((size_t)p * KSUSP + sid) * DFS_SAVE_STRIDE;
+        uint32_t *sbase = B.susp + (size_t)p * KSUSP * DFS_SAVE_STRIDE;
+        const bool resume = sid_in >= 0;
+        if (resume) {
+            const uint32_t *src = sbase + (size_t)sid_in * DFS_SAVE_STRIDE;
             for (int w = lane; w < DFS_SAVE_WORDS; w += 32) reinterpret_cast<uint32_t *>(&W)[w] = src[w];
             __syncwarp();
         }
         uint32_t steps = 0;
         int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
-        if (r == DFS_SUSPENDED && sid < 0) {
-            int got = -1;
-            if (lane == 0) {  // claim a free saved-state slot of this pattern
-                unsigned int *m = &B.st[p].susp_mask;
-                unsigned int cur = atomicAdd(m, 0u);
-                for (int tries = 0; tries < 64 && got < 0; tries++) {
-                    const unsigned int freeb = ~cur & ((1u << KSUSP) - 1u);
-                    if (!freeb) break;
-                    const int b = __ffs(freeb) - 1;
-                    const unsigned int prev = atomicCAS(m, cur, cur | (1u << b));
-                    if (prev == cur) got = b; else cur = prev;
+        int sidA = sid_in;
+        if (r == DFS_SUSPENDED) {
+            const bool head = !resume || seq[0] == sid_in;
+            // split level: the shallowest level this search may still rebind that has unscanned
+            // candidates (shallow candidates carry the largest subtrees)
+            int m = -1;
+            for (int l = W.floor; l <= W.level; l++)
+                if (W.pos[l] < W.hi[l]) { m = l; break; }
+            const int pieces = (head && m >= 0) ? (int)min(W.hi[m] - W.pos[m], (uint32_t)SPLIT_MAX) : 0;
+            unsigned int got = 0;
+            if (lane == 0) {
+                const int want = (resume ? 0 : 1) + (pieces > 0 ? pieces + 1 : 0);
+                got = want ? claim_sids(&B.st[p].susp_mask, want) : 0u;
+            }
+            got = __shfl_sync(FULLMASK, got, 0);
+            if (!resume) {
+                if (!got) {
+                    r = dfs_run(B.G, W, used, root, bytes, probes, steps, 0, true);  // no room: finish
+                } else {
+                    sidA = __ffs(got) - 1;
+                    got &= got - 1;
                 }
             }
-            sid = __shfl_sync(FULLMASK, got, 0);
-            if (sid < 0) r = dfs_run(B.G, W, used, root, bytes, probes, steps, 0, true);  // no room
+            if (r == DFS_SUSPENDED) {
+                const int np = __popc(got) >= 2 ? min(pieces, __popc(got) - 1) : 0;
+                unsigned int keep = 0, g1 = got;  // sids of the split: np pieces + the continuation
+                for (int k = 0; k < (np ? np + 1 : 0); k++) {
+                    const unsigned int b = g1 & (~g1 + 1u);
+                    keep |= b;
+                    g1 &= ~b;
+                }
+                if (lane == 0 && (got & ~keep)) atomicAnd(&B.st[p].susp_mask, ~(got & ~keep));
+                const int32_t old_next = resume ? (int32_t)sbase[(size_t)sidA * DFS_SAVE_STRIDE + SUSP_NEXT] : -1;
+                int32_t link = sidA;  // last sub-search of the new chain so far
+                if (np > 0) {
+                    const uint32_t a = W.pos[m], b = W.hi[m], len = b - a;
+                    const int lvl0 = W.level, floor0 = W.floor;
+                    const uint32_t mask_m = W.mask[m], conf_m = W.conf[m];
+                    unsigned int g2 = keep;
+                    for (int j = 0; j <= np; j++) {
+                        const int sid = __ffs(g2) - 1;
+                        g2 &= g2 - 1;
+                        if (lane == 0) {
+                            W.level = m;
+                            W.mask[m] = 0;
+                            if (j < np) {  // piece j: candidates [a + len*j/np, a + len*(j+1)/np) of level m
+                                W.floor = m;
+                                W.pos[m] = a + (uint32_t)((uint64_t)len * j / np);
+                                W.hi[m] = a + (uint32_t)((uint64_t)len * (j + 1) / np);
+                                W.conf[m] = 0;
+                            } else {  // continuation: level m exhausted, plain backtracking below it
+                                W.floor = floor0;
+                                W.pos[m] = b;
+                                W.hi[m] = b;
+                                W.conf[m] = (1u << m) - 1u;
+                            }
+                        }
+                        __syncwarp();
+                        save_state(sbase + (size_t)sid * DFS_SAVE_STRIDE, W, SS_PENDING);
+                        if (lane == 0) sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)sid;
+                        link = sid;
+                    }
+                    if (lane == 0) {  // the head keeps what it had scanned of level m, nothing more
+                        W.level = lvl0;
+                        W.floor = m;
+                        W.pos[m] = a;
+                        W.hi[m] = a;
+                        W.mask[m] = mask_m;
+                        W.conf[m] = conf_m;
+                    }
+                    __syncwarp();
+                }
+                save_state(sbase + (size_t)sidA * DFS_SAVE_STRIDE, W, SS_PENDING);
+                if (lane == 0) {
+                    if (np == 0) sbase[(size_t)sidA * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
+                    else sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
+                    if (!resume) {
+                        seq[0] = sidA;
+                        B.win_state[slot] = SLOT_SEQ;
+                    }
+                }
+                __syncwarp();
+            }
         }
         if (lane == 0 && steps) {
             atomicAdd(&B.st[p].steps, (unsigned long long)steps);
             atomicMax(&B.st[p].max_steps, steps);
         }
-        if (r == DFS_SUSPENDED) {
-            uint32_t *dst = B.susp + ((size_t)p * KSUSP + sid) * DFS_SAVE_STRIDE;
-            for (int w = lane; w < DFS_SAVE_WORDS; w += 32) dst[w] = reinterpret_cast<const uint32_t *>(&W)[w];
-            if (lane == 0) {
-                B.win_state[slot] = SLOT_SUSPENDED;
-                B.win_map[slot * MAXN] = sid;
+        if (r != DFS_SUSPENDED) {
+            if (!resume) {
+                if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
+                if (r == DFS_FOUND && lane < P.n) seq[lane] = W.t[lane];
+            } else {  // the state is kept so that the sub-search can go on past its map
+                save_state(sbase + (size_t)sid_in * DFS_SAVE_STRIDE, W, r == DFS_FOUND ? SS_FOUND : SS_NONE);
             }
-        } else {
-            if (sid >= 0 && lane == 0) atomicAnd(&B.st[p].susp_mask, ~(1u << sid));
-            if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
-            if (r == DFS_FOUND && lane < P.n) B.win_map[slot * MAXN + lane] = W.t[lane];
         }
         __syncwarp();
     }
@@ -540,6 +654,60 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     const int32_t *st_cur = B.win_state + cb, *rt_cur = B.win_root + cb, *mp_cur = B.win_map + cb * MAXN;
     int32_t *st_nxt = B.win_state + nb, *rt_nxt = B.win_root + nb, *mp_nxt = B.win_map + nb * MAXN;
     uint32_t *used = B.used + (size_t)p * B.G.words;
+    uint32_t *sbase = B.susp + (size_t)p * KSUSP * DFS_SAVE_STRIDE;
+
+    // 0. sub-search sequences: drop sub-searches that found nothing; a slot whose first
+    //    remaining sub-search found a map takes that map (if a vertex of it has been used since,
+    //    the sub-search goes on from there instead); a slot with none left has no map
+    for (int s = tid; s < nwin; s += nthr) {
+        if (st_cur[s] != SLOT_SEQ) continue;
+        int32_t *sq = const_cast<int32_t *>(mp_cur) + (size_t)s * MAXN;
+        int state = SLOT_SEQ;
+        int32_t head = -1, last = -1;
+        unsigned int release = 0;
+        int32_t cur_sid = sq[0];
+        for (int guard = 0; cur_sid >= 0 && guard < KSUSP; guard++) {
+            uint32_t *e = sbase + (size_t)cur_sid * DFS_SAVE_STRIDE;
+            const int32_t next = (int32_t)e[SUSP_NEXT];
+            int status = (int)e[SUSP_STATUS];
+            if (status == SS_FOUND && head < 0) {
+                bool stale = false;
+                for (int l = 0; l < n; l++) stale |= used_bit(used, (int32_t)e[SUSP_MAP + l]);
+                if (stale) {
+                    e[SUSP_STATUS] = SS_PENDING;
+                    status = SS_PENDING;
+                } else {
+                    release |= 1u << cur_sid;  // this and every later sub-search are done with
+                    for (int32_t r2 = next, g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
+                        release |= 1u << r2;
+                        r2 = (int32_t)sbase[(size_t)r2 * DFS_SAVE_STRIDE + SUSP_NEXT];
+                    }
+                    for (int l = 0; l < n; l++) sq[l] = (int32_t)e[SUSP_MAP + l];
+                    state = SLOT_MAP;
+                    break;
+                }
+            }
+            if (status == SS_NONE) {
+                release |= 1u << cur_sid;
+            } else {
+                if (head < 0) head = cur_sid;
+                else sbase[(size_t)last * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)cur_sid;
+                last = cur_sid;
+            }
+            cur_sid = next;
+        }
+        if (state == SLOT_SEQ) {
+            if (head < 0) {
+                state = SLOT_NONE;
+            } else {
+                sbase[(size_t)last * DFS_SAVE_STRIDE + SUSP_NEXT] = 0xFFFFFFFFu;
+                sq[0] = head;
+            }
+        }
+        if (release) atomicAnd(&S->susp_mask, ~release);
+        const_cast<int32_t *>(st_cur)[s] = state;
+    }
+    __syncthreads();
 
     // 1. horizon: index of the (KMAP+1)-th map slot (or the window end)
     if (tid == 0) s_horizon = nwin;
@@ -592,7 +760,7 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     }
     // a suspended search is undecided: nothing at or after it can be committed yet
     for (int s = tid; s < horizon; s += nthr)
-        if (st_cur[s] == SLOT_SUSPENDED) atomicMin(&s_f, s);
+        if (st_cur[s] == SLOT_SEQ) atomicMin(&s_f, s);
     __syncthreads();
     const int f = s_f;
     // 4. commit the map slots before f, in slot order
@@ -632,8 +800,8 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
                     mp_nxt[(size_t)r * MAXN + l] = m[l];
                     if (owner(m[l]) < f) state = SLOT_NEEDS;
                 }
-            } else if (state == SLOT_SUSPENDED) {
-                mp_nxt[(size_t)r * MAXN] = mp_cur[(size_t)s * MAXN];  // saved-state index
+            } else if (state == SLOT_SEQ) {
+                for (int l = 0; l < MAXN; l++) mp_nxt[(size_t)r * MAXN + l] = mp_cur[(size_t)s * MAXN + l];
             }
             rt_nxt[r] = rt_cur[s];
             st_nxt[r] = state;
@@ -673,22 +841,46 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     }
     // 8. one search item for every slot that needs a map
     __syncthreads();
+    // items: a fresh search per NEEDS slot, one continuation per pending sub-search of a SEQ slot
+    auto n_items_of = [&](int s) -> int {
+        if (s >= nw) return 0;
+        const int st = st_nxt[s];
+        if (st == SLOT_NEEDS) return 1;
+        if (st != SLOT_SEQ) return 0;
+        int c = 0;
+        for (int32_t r2 = mp_nxt[(size_t)s * MAXN], g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
+            const uint32_t *e = sbase + (size_t)r2 * DFS_SAVE_STRIDE;
+            c += (int)(e[SUSP_STATUS] == SS_PENDING);
+            r2 = (int32_t)e[SUSP_NEXT];
+        }
+        return c;
+    };
     int nitems = 0;
     for (int b0 = 0; b0 < nw; b0 += nthr) {
-        const int s = b0 + tid;
         int excl;
-        nitems += block_scan((s < nw && (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_SUSPENDED)) ? 1 : 0,
-                             excl, sh_scan);
+        nitems += block_scan(n_items_of(b0 + tid), excl, sh_scan);
     }
     if (tid == 0) s_base = nitems ? atomicAdd(&B.ctl->n_items[q], nitems) : 0;
     __syncthreads();
     int wr = s_base;
     for (int b0 = 0; b0 < nw; b0 += nthr) {
         const int s = b0 + tid;
-        const int nd = (s < nw && (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_SUSPENDED)) ? 1 : 0;
+        const int nd = n_items_of(s);
         int excl;
         const int tot = block_scan(nd, excl, sh_scan);
-        if (nd) B.items[wr + excl] = make_int2(p, nxt * Wmax + s);
+        if (nd) {
+            const int o = nxt * Wmax + s;
+            if (st_nxt[s] == SLOT_NEEDS) {
+                B.items[wr + excl] = make_int2(p, o);
+            } else {
+                int w = wr + excl;
+                for (int32_t r2 = mp_nxt[(size_t)s * MAXN], g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
+                    const uint32_t *e = sbase + (size_t)r2 * DFS_SAVE_STRIDE;
+                    if (e[SUSP_STATUS] == SS_PENDING) B.items[w++] = make_int2(p, o | ((r2 + 1) << 24));
+                    r2 = (int32_t)e[SUSP_NEXT];
+                }
+            }
+        }
         wr += tot;
     }
     if (tid == 0) {
@@ -900,7 +1092,7 @@ static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &by
 static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
 
 int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes) {
-    *bytes = (int64_t)g->view.words * 4 + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) +
+    *bytes = (int64_t)g->view.words * 4 + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) + 8 * KSUSP +
              (int64_t)sizeof(PatState) + (int64_t)sizeof(Plan) + (int64_t)sizeof(flexis_support_result) +
              8 * (MAXN + 1) + (int64_t)sel * 4 * MAXN + 4ll * KSUSP * DFS_SAVE_STRIDE;
     return FLEXIS_OK;
@@ -975,7 +1167,7 @@ static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax
     CK(alloc((void **)&w.win_root, sizeof(int32_t) * (size_t)nSlots * 2));
     CK(alloc((void **)&w.win_state, sizeof(int32_t) * (size_t)nSlots * 2));
     CK(alloc((void **)&w.win_map, sizeof(int32_t) * (size_t)nSlots * 2 * MAXN));
-    CK(alloc((void **)&w.items, sizeof(int2) * (size_t)nSlots));
+    CK(alloc((void **)&w.items, sizeof(int2) * ((size_t)nSlots + (size_t)nP * KSUSP)));
     CK(alloc((void **)&w.ctl, sizeof(Ctl)));
     CK(alloc((void **)&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
     CK(alloc((void **)&w.susp, sizeof(uint32_t) * (size_t)nP * KSUSP * DFS_SAVE_STRIDE));
@@ -1187,7 +1379,7 @@ static NoallocLayout noalloc_layout(int64_t words) {
     L.plan = take(sizeof(Plan));
     L.result = take(sizeof(flexis_support_result));
     L.mni_seg = take(sizeof(unsigned long long) * (MAXN + 1));
-    L.items = take(sizeof(int2) * NOALLOC_WMAX);
+    L.items = take(sizeof(int2) * (NOALLOC_WMAX + KSUSP));
     L.win_root = take(sizeof(int32_t) * 2 * NOALLOC_WMAX);
     L.win_state = take(sizeof(int32_t) * 2 * NOALLOC_WMAX);
     L.win_map = take(sizeof(int32_t) * 2 * NOALLOC_WMAX * MAXN);
