@@ -84,7 +84,10 @@ typedef struct {
     int32_t record_selected; /* >0: keep up to this many selected maps per pattern (tests) */
     int32_t search_budget;   /* candidate chunks a root search runs per round before it is
                                 suspended and resumed in the next round: 0 = default, -1 = never */
-    int32_t reserved[8];
+    int32_t split_pieces;    /* pieces a suspended search heading its slot is split into per round:
+                                0 = default, -1 = never split */
+    int32_t sub_searches;    /* saved sub-searches a pattern may hold at once (1..32): 0 = default */
+    int32_t reserved[6];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

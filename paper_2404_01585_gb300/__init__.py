@@ -46,7 +46,7 @@ class flexis_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("device", C.c_int32), ("window_min", C.c_int32),
                 ("window_max", C.c_int32), ("search_blocks", C.c_int32),
                 ("record_selected", C.c_int32), ("search_budget", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class flexis_pattern(C.Structure):

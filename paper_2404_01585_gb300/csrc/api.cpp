@@ -94,6 +94,8 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.rounds_per_sync = P >= 64 ? 4 : 2;
     c.timing = g->opt.reserved[0] != 0;
     c.search_budget = g->opt.search_budget;
+    c.split_pieces = g->opt.split_pieces;
+    c.sub_searches = g->opt.sub_searches;
     return c;
 }
 

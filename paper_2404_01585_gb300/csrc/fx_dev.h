@@ -15,6 +15,8 @@ struct EvalConfig {
     int32_t record_selected = 0;
     int32_t rounds_per_sync = 4;
     int32_t search_budget = 0;  // 0: default per-round budget; < 0: unlimited
+    int32_t split_pieces = 0;   // 0: default pieces per split; < 0: never split
+    int32_t sub_searches = 0;   // 0: default saved sub-searches per pattern
     bool timing = false;        // per-launch CUDA events around the search kernel
 };
 

@@ -103,6 +103,8 @@ struct Batch {
     int32_t Wmin;
     int32_t sel_cap;
     uint32_t budget;      // per-round candidate chunks of one root search (0: unlimited)
+    int32_t split_max;    // pieces per split (0: no split)
+    uint32_t sid_all;     // saved sub-search indices a pattern may use (bit set)
     PatState *st;
     uint32_t *used;       // [P][words]
     int32_t *win_root;    // [P][2][Wmax]  two window buffers per pattern
@@ -427,10 +429,9 @@ __global__ void k_admit(Batch B, const int32_t *slots, int n) {
 __global__ void k_reset_ctl(Batch B) { reset_ctl(B.ctl); }
 
 // Claim up to `want` free saved-sub-search indices of a pattern; returns them as a bit set.
-__device__ unsigned int claim_sids(unsigned int *m, int want) {
+__device__ unsigned int claim_sids(unsigned int *m, int want, unsigned int ALL) {
     unsigned int cur = atomicAdd(m, 0u);
     for (int tries = 0; tries < 64; tries++) {
-        constexpr unsigned int ALL = KSUSP >= 32 ? 0xFFFFFFFFu : ((1u << (KSUSP & 31)) - 1u);
         unsigned int freeb = ~cur & ALL, take = 0;
         for (int k = 0; k < want && freeb; k++) {
             const unsigned int b = freeb & (~freeb + 1u);
@@ -497,11 +498,11 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             int m = -1;
             for (int l = W.floor; l <= W.level; l++)
                 if (W.pos[l] < W.hi[l]) { m = l; break; }
-            const int pieces = (head && m >= 0) ? (int)min(W.hi[m] - W.pos[m], (uint32_t)SPLIT_MAX) : 0;
+            const int pieces = (head && m >= 0) ? (int)min(W.hi[m] - W.pos[m], (uint32_t)B.split_max) : 0;
             unsigned int got = 0;
             if (lane == 0) {
                 const int want = (resume ? 0 : 1) + (pieces > 0 ? pieces + 1 : 0);
-                got = want ? claim_sids(&B.st[p].susp_mask, want) : 0u;
+                got = want ? claim_sids(&B.st[p].susp_mask, want, B.sid_all) : 0u;
             }
             got = __shfl_sync(FULLMASK, got, 0);
             if (!resume) {
@@ -1214,6 +1215,8 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
     B.Wmin = Wmin;
     B.sel_cap = sel;
     B.budget = SEARCH_BUDGET;
+    B.split_max = SPLIT_MAX;
+    B.sid_all = KSUSP >= 32 ? 0xFFFFFFFFu : ((1u << (KSUSP & 31)) - 1u);
     B.st = w.st;
     B.used = w.used;
     B.win_root = w.win_root;
@@ -1248,6 +1251,11 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     g->last_sel = cfg.record_selected;
     Batch B = make_batch(g, w, d_plans, P, Wmin, Wmax, cfg.record_selected, d_results);
     if (cfg.search_budget != 0) B.budget = cfg.search_budget < 0 ? 0u : (uint32_t)cfg.search_budget;
+    if (cfg.split_pieces != 0) B.split_max = cfg.split_pieces < 0 ? 0 : std::min(cfg.split_pieces, SPLIT_MAX);
+    if (cfg.sub_searches > 0) {
+        const int k = std::min(cfg.sub_searches, KSUSP);
+        B.sid_all = k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1u);
+    }
     const size_t smem = commit_smem(Wmax);
     const int sblocks = search_grid(g, cfg);
 
@@ -1436,6 +1444,8 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
     B.Wmin = 256;
     B.sel_cap = 0;
     B.budget = SEARCH_BUDGET;
+    B.split_max = SPLIT_MAX;
+    B.sid_all = KSUSP >= 32 ? 0xFFFFFFFFu : ((1u << (KSUSP & 31)) - 1u);
     B.st = reinterpret_cast<PatState *>(base + L.st);
     B.used = reinterpret_cast<uint32_t *>(base + L.used);
     B.win_root = reinterpret_cast<int32_t *>(base + L.win_root);
