@@ -85,6 +85,7 @@ struct Ctl {
     int32_t n_items[2];
     int32_t next_item[2];
     int32_t active[2];
+    int32_t acount[2];    // lengths of the two active-pattern lists
     int32_t err;
     int32_t pad;
     unsigned long long bytes_greedy;
@@ -114,6 +115,7 @@ struct Batch {
     Ctl *ctl;
     int32_t *sel;         // [P][sel_cap][8] selected maps, canonical vertex order
     unsigned long long *mni_seg;  // [P*8+1] prefix sums of MNI candidate segments
+    int32_t *alist;               // [2][P] patterns still in their greedy phase (nullable: all)
     uint32_t *susp;               // [P][KSUSP][DFS_SAVE_STRIDE] saved search states
     flexis_support_result *results;
 };
@@ -141,7 +143,7 @@ constexpr int SUSP_NEXT = DFS_SAVE_WORDS + 1;    // next sub-search of the same 
 constexpr int SUSP_MAP = DFS_SAVE_WORDS + 2;     // its map (by level) when SS_FOUND
 static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large");
 constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
-constexpr uint32_t SEARCH_BUDGET = 2048;  // candidate chunks a root search runs per round
+constexpr uint32_t SEARCH_BUDGET = 8192;  // candidate chunks a root search runs per round
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
@@ -410,11 +412,13 @@ __device__ void init_slot(const Batch &B, int p) {
     B.st[p] = s;
 }
 
-// closed batch: every slot [0, P) starts
+// closed batch: every slot [0, P) starts (the control words are zeroed before the launch); with
+// an active list, the patterns that have a greedy phase form list 0
 __global__ void k_init(Batch B) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) reset_ctl(B.ctl);
-    if (p < B.P) init_slot(B, p);
+    if (p >= B.P) return;
+    init_slot(B, p);
+    if (B.alist && B.st[p].phase == PH_GREEDY) B.alist[atomicAdd(&B.ctl->acount[0], 1)] = p;
 }
 
 // serving: (re)start the listed slots and clear their used bitmaps; one block per slot
@@ -464,6 +468,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     const int lane = threadIdx.x & 31;
     WarpState &W = ws[threadIdx.x >> 5];
     const int n_items = *reinterpret_cast<volatile int32_t *>(&B.ctl->n_items[q]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->acount[q] = 0;  // list q has been consumed
     unsigned long long bytes = 0;
     uint32_t probes = 0;
     for (;;) {
@@ -627,22 +632,15 @@ __device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
     return ((uint32_t)v * 0x9E3779B1u) >> (32 - logT);
 }
 
-// One block per pattern: inverted index of the window's maps, prefix commit, refill, new items.
-// The window lives in two global buffers per pattern; the kept slots and the refill go to the
-// other buffer, which becomes current for the next search.
-__global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
-    extern __shared__ int32_t smem[];
+// Commit of one pattern by one block: inverted index of the window's maps, prefix commit, refill,
+// new items.  The window lives in two global buffers per pattern; the kept slots and the refill go
+// to the other buffer, which becomes current for the next search.
+__device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t *smem) {
     int32_t *keys = smem, *vals = smem + COMMIT_HASH;
     __shared__ int sh_scan[40];
     __shared__ int s_f, s_newcur, s_horizon, s_base;
-    const int p = blockIdx.x;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
-    if (p == 0 && tid == 0) {
-        B.ctl->n_items[q ^ 1] = 0;
-        B.ctl->next_item[q ^ 1] = 0;
-        B.ctl->active[q ^ 1] = 0;
-    }
     PatState *S = B.st + p;
     if (S->phase != PH_GREEDY) return;
     const Plan &P = B.plans[p];
@@ -902,8 +900,30 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
             S->phase = PH_MNI;
         } else {
             atomicAdd(&B.ctl->active[q], 1);
+            if (B.alist) B.alist[(size_t)(q ^ 1) * B.P + atomicAdd(&B.ctl->acount[q ^ 1], 1)] = p;
         }
         if (nitems) atomicAdd(&B.ctl->search_items, (unsigned long long)nitems);
+    }
+}
+
+// Dense form: one block per pattern slot.  Listed form: blocks walk the list of patterns still in
+// their greedy phase (so late rounds of a large batch launch no block per finished pattern), and
+// append the patterns that stay active to the other list.
+__global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
+    extern __shared__ int32_t smem[];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B.ctl->n_items[q ^ 1] = 0;
+        B.ctl->next_item[q ^ 1] = 0;
+        B.ctl->active[q ^ 1] = 0;
+    }
+    if (!B.alist) {
+        commit_one(B, q, blockIdx.x, smem);
+        return;
+    }
+    const int count = *reinterpret_cast<volatile int32_t *>(&B.ctl->acount[q]);
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        commit_one(B, q, B.alist[(size_t)q * B.P + i], smem);
+        __syncthreads();
     }
 }
 
@@ -1062,6 +1082,7 @@ struct Workspace {
     int32_t *sel_buf = nullptr;
     unsigned long long *mni_seg = nullptr;
     uint32_t *susp = nullptr;
+    int32_t *alist = nullptr;
     Plan *plans = nullptr;                   // device plan array (host-plan entry points)
     flexis_support_result *results = nullptr;
     int32_t plans_cap = 0;
@@ -1141,7 +1162,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
 static void ws_free(Workspace &w) {
     cudaFree(w.st); cudaFree(w.used); cudaFree(w.win_root); cudaFree(w.win_state);
     cudaFree(w.win_map); cudaFree(w.items); cudaFree(w.ctl); cudaFree(w.sel_buf);
-    cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results); cudaFree(w.susp);
+    cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results); cudaFree(w.susp); cudaFree(w.alist);
     if (w.h_ctl) cudaFreeHost(w.h_ctl);
     w = Workspace();
 }
@@ -1172,6 +1193,7 @@ static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax
     CK(alloc((void **)&w.ctl, sizeof(Ctl)));
     CK(alloc((void **)&w.mni_seg, sizeof(unsigned long long) * ((size_t)nP * MAXN + 1)));
     CK(alloc((void **)&w.susp, sizeof(uint32_t) * (size_t)nP * KSUSP * DFS_SAVE_STRIDE));
+    CK(alloc((void **)&w.alist, sizeof(int32_t) * (size_t)nP * 2));
     CK(alloc((void **)&w.plans, sizeof(Plan) * (size_t)nP));
     CK(alloc((void **)&w.results, sizeof(flexis_support_result) * (size_t)nP));
     if (nSel > 0) CK(alloc((void **)&w.sel_buf, sizeof(int32_t) * (size_t)nSel * MAXN));
@@ -1227,6 +1249,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
     B.sel = sel > 0 ? w.sel_buf : nullptr;
     B.mni_seg = w.mni_seg;
     B.susp = w.susp;
+    B.alist = nullptr;  // dense: every slot of the batch is visited by the commit kernel
     B.results = results;
     return B;
 }
@@ -1250,6 +1273,10 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     g->last_P = P;
     g->last_sel = cfg.record_selected;
     Batch B = make_batch(g, w, d_plans, P, Wmin, Wmax, cfg.record_selected, d_results);
+    // large batches walk a list of the patterns still active; small ones launch a block per slot
+    const int list_threshold = 4 * g->sm_count;
+    if (P > list_threshold) B.alist = w.alist;
+    const int commit_blocks = P > list_threshold ? list_threshold : P;
     if (cfg.search_budget != 0) B.budget = cfg.search_budget < 0 ? 0u : (uint32_t)cfg.search_budget;
     if (cfg.split_pieces != 0) B.split_max = cfg.split_pieces < 0 ? 0 : std::min(cfg.split_pieces, SPLIT_MAX);
     if (cfg.sub_searches > 0) {
@@ -1262,6 +1289,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     int64_t launches = 0;
     CK(cudaEventRecord(g->ev[0], stream));
     CK(cudaMemsetAsync(w.used, 0, sizeof(uint32_t) * (size_t)g->view.words * P, stream));
+    CK(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), stream));
     k_init<<<(P + 255) / 256, 256, 0, stream>>>(B);
     launches += 1;
     int64_t rounds = 0;
@@ -1271,7 +1299,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     for (;;) {
         for (int r = 0; r < R; r++) {
             const int q = (int)(rounds & 1);
-            k_commit<<<P, COMMIT_THREADS, smem, stream>>>(B, q);
+            k_commit<<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
             if (cfg.timing) {
                 while (evi + 2 > g->sev.size()) {
                     cudaEvent_t e;
@@ -1461,6 +1489,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
     // pattern state and control words are rewritten by k_init)
     CK(cudaMemcpyAsync(base + L.plan, h_plan, sizeof(Plan), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(B.used, 0, sizeof(uint32_t) * (size_t)g->view.words, stream));
+    CK(cudaMemsetAsync(B.ctl, 0, sizeof(Ctl), stream));
     k_init<<<1, 256, 0, stream>>>(B);
     const int sblocks = g->sm_count * 6;
     Ctl h_ctl;

@@ -252,3 +252,16 @@ def test_no_mni_mode(powerlaw):
         assert (r["tau"], r["mis"], bool(r["frequent"])) == (w["tau"], w["mis"], w["frequent"])
         assert r["mni"] == -1 and r["flags"] & fx.FLEXIS_FLAG_MNI_SKIPPED
     g.close()
+
+
+def test_large_batch_active_list():
+    # more patterns than the dense-commit threshold (4 blocks per SM): the commit kernel walks the
+    # list of patterns still in their greedy phase
+    lab, src, dst = make_graph(kind="cl", nv=4000, ne=16000, nl=5, law="zipf", zipf_s=1.0, gamma=2.3,
+                               seed=61)
+    pats = random_patterns(1500, range(2, 6), SHAPES, lab, 63)
+    og = oracle.Graph(lab, src, dst)
+    for opts in ({}, dict(search_budget=2, window_max=64)):
+        g = fx.Graph(lab, src, dst, **opts)
+        check_batch(g, og, pats, 20, 0.5, EARLY)
+        g.close()
