@@ -1229,7 +1229,7 @@ int dev_graph_props(const DeviceGraph *g, int *sm, int *l2) {
 
 static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *plans, int32_t P,
                         int Wmin, int Wmax, int sel, flexis_support_result *results) {
-    Batch B;
+    Batch B{};  // every field zero (null pointers) unless set below
     B.G = g->view;
     B.plans = plans;
     B.P = P;
@@ -1464,7 +1464,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
     int rc = noalloc_base(g->device, &base);
     if (rc) return rc;
     if (!stream) stream = g->stream;
-    Batch B;
+    Batch B{};  // every field zero (null pointers: no active list, no selection log) unless set below
     B.G = g->view;
     B.plans = reinterpret_cast<const Plan *>(base + L.plan);
     B.P = 1;
