@@ -277,7 +277,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // every popped candidate is re-tested against the used set.  Everything skipped before the
 // suspension failed under the smaller used set and fails under the larger one, so the first map
 // found is the first map avoiding the current used set.
-enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2 };
+enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
 
 __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                        unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             got = __shfl_sync(FULLMASK, got, 0);
             if (!resume) {
                 if (!got) {
-                    r = dfs_run(B.G, W, used, root, bytes, probes, steps, 0, true);  // no room: finish
+                    // no free saved-state slot: the slot stays NEEDS (undecided) and its search
+                    // starts over next round, when earlier sub-searches have released slots
+                    r = DFS_NOROOM;
                 } else {
                     sidA = __ffs(got) - 1;
                     got &= got - 1;
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             atomicAdd(&B.st[p].steps, (unsigned long long)steps);
             atomicMax(&B.st[p].max_steps, steps);
         }
-        if (r != DFS_SUSPENDED) {
+        if (r == DFS_FOUND || r == DFS_NONE) {
             if (!resume) {
                 if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
                 if (r == DFS_FOUND && lane < P.n) seq[lane] = W.t[lane];
@@ -757,9 +759,10 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         if (st_cur[s] != SLOT_MAP) continue;
         if (owner(mp_cur[(size_t)s * MAXN + k]) < s) atomicMin(&s_f, s);
     }
-    // a suspended search is undecided: nothing at or after it can be committed yet
+    // a suspended search, or one that found no room to be suspended and starts over, is
+    // undecided: nothing at or after it can be committed yet
     for (int s = tid; s < horizon; s += nthr)
-        if (st_cur[s] == SLOT_SEQ) atomicMin(&s_f, s);
+        if (st_cur[s] == SLOT_SEQ || st_cur[s] == SLOT_NEEDS) atomicMin(&s_f, s);
     __syncthreads();
     const int f = s_f;
     // 4. commit the map slots before f, in slot order
