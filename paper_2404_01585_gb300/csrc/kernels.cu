@@ -143,7 +143,7 @@ constexpr int SUSP_NEXT = DFS_SAVE_WORDS + 1;    // next sub-search of the same 
 constexpr int SUSP_MAP = DFS_SAVE_WORDS + 2;     // its map (by level) when SS_FOUND
 static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large");
 constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
-constexpr uint32_t SEARCH_BUDGET = 8192;  // candidate chunks a root search runs per round
+constexpr uint32_t SEARCH_BUDGET = 4096;  // candidate chunks a root search runs per round
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
