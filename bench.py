@@ -31,6 +31,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -135,6 +137,53 @@ def run_oracle_sample(lab, src, dst):
     desc = (f"oracle tier-1 mining of the same graph, (sigma, lambda) in {ORACLE_SAMPLE['runs']}, "
             f"max_edges={ORACLE_SAMPLE['max_edges']} (levels 2..4): {cand} supports")
     return cand, dt, desc
+
+
+def serving_leg(g, fx, lab, nq=300, rates=(0.3, 0.6, 0.9), seed=2005):
+    """Continuous-batching serving on the resident graph: a Poisson stream of support queries
+    (pattern of 3-8 vertices: random tree / cycle / clique with labels from the graph's label
+    distribution; sigma in {1000, 5000, 20000}; lambda in {0, 0.5, 1}; EARLY, mIS decision) at
+    three arrival rates, each a fraction of the saturated batch throughput of the same queries.
+    Latency = submit -> result, measured by the server."""
+    from workloads import Stream, random_patterns
+    pats = random_patterns(nq, range(3, 9), ["tree", "cycle", "clique"], lab, seed)
+    st = Stream(seed + 1)
+    sig = [int((1000, 5000, 20000)[int(x)]) for x in st.integers(nq, 3)]
+    lam = [float((0.0, 0.5, 1.0)[int(x)]) for x in st.integers(nq, 3)]
+    mode = fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI
+    t0 = time.perf_counter()
+    g.support_batch(pats, sig, lam, mode)
+    sat = nq / (time.perf_counter() - t0)
+    out = {"queries_per_rate": nq, "saturated_batch_qps": sat,
+           "workload": "Poisson stream, patterns 3-8 vertices (tree/cycle/clique), "
+                       "sigma {1000,5000,20000} x lambda {0,0.5,1}, EARLY mIS decision", "rates": []}
+    for frac in rates:
+        rate = frac * sat
+        nr = min(nq, max(60, int(20 * rate)))  # about 20 s of arrivals per rate at most
+        gaps = -np.log(1.0 - st.uniform(nr)) / rate
+        srv = fx.Server(g, slots=256)
+        lat, done = {}, 0
+        start = time.perf_counter()
+        due = start + np.cumsum(gaps)
+        for i in range(nr):
+            while time.perf_counter() < due[i]:
+                for rid, r, us in srv.poll():
+                    lat[rid] = us
+                time.sleep(0.0002)
+            while srv.submit(i, pats[i][0], pats[i][1], sig[i], lam[i], mode) == fx.FLEXIS_E_BUSY:
+                time.sleep(0.001)
+        while len(lat) < nr and time.perf_counter() - start < 180:
+            for rid, r, us in srv.poll():
+                lat[rid] = us
+            time.sleep(0.0005)
+        end = time.perf_counter()
+        srv.stop()
+        L = sorted(lat.values())
+        out["rates"].append({"arrival_fraction_of_saturated": frac, "offered_qps": rate,
+                             "submitted": nr, "completed": len(L), "achieved_qps": len(L) / (end - start),
+                             "p50_ms": L[len(L) // 2] / 1e3 if L else None,
+                             "p99_ms": L[min(len(L) - 1, int(len(L) * 0.99))] / 1e3 if L else None})
+    return out
 
 
 def reference_arm(args):
@@ -310,6 +359,8 @@ def main():
            "plain_supports_per_s": len(sample) / sum(lat),
            "plain_p50_ms": 1e3 * lat[len(lat) // 2], "plain_p99_ms": 1e3 * lat[min(len(lat) - 1, int(len(lat) * 0.99))]}
 
+    serving = serving_leg(g, fx, lab) if rank == 0 and not args.skip_extras else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c, t, desc = run_oracle_sample(lab, src, dst)
@@ -324,7 +375,7 @@ def main():
                                        "supports_per_step": total_c // args.steps}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(stats.get("kernel_launches", 0)), "clocks": clk,
-                "batched_vs_plain": bvp,
+                "batched_vs_plain": bvp, "serving": serving,
                 "kernel_time_ms": {"search": stats["search_ms"], "device_total": stats["total_ms"],
                                    "host_candidate_generation": stats["host_gen_ms"],
                                    "host_compile": stats["host_compile_ms"]}}

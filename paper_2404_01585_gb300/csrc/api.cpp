@@ -80,7 +80,11 @@ void add_stats(flexis_stats &a, const flexis_stats &b) {
 
 // Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism
 // comes from the batch, and per-pattern window memory stays small); few patterns -> large
-// windows (parallelism has to come from speculation inside each pattern).
+// windows (parallelism has to come from speculation inside each pattern).  Few patterns also
+// get a small per-round search budget, so that heavy searches are split early and spread
+// over the idle warps; a large batch already fills the GPU and keeps the default.
+constexpr int32_t SMALL_BATCH = 1024, SMALL_BATCH_BUDGET = 256;
+
 EvalConfig config_for(const flexis_graph *g, int32_t P) {
     EvalConfig c;
     int wmax = P < 64 ? 8192 : P < 4096 ? 4096 : P < 65536 ? 1024 : 512;
@@ -93,7 +97,7 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.record_selected = g->opt.record_selected;
     c.rounds_per_sync = P >= 64 ? 4 : 2;
     c.timing = g->opt.reserved[0] != 0;
-    c.search_budget = g->opt.search_budget;
+    c.search_budget = g->opt.search_budget != 0 ? g->opt.search_budget : P < SMALL_BATCH ? SMALL_BATCH_BUDGET : 0;
     c.split_pieces = g->opt.split_pieces;
     c.sub_searches = g->opt.sub_searches;
     return c;
@@ -550,13 +554,13 @@ int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out) {
         cudaSetDevice(dev_graph_device(g->dg));
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return FLEXIS_E_CUDA;
         int64_t per = 1;
-        serve_slot_bytes(g->dg, &per);
+        serve_slot_bytes(g->dg, g->opt.window_max, &per);
         slots = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(fr / 4) / std::max<int64_t>(per, 1)));
     }
     std::unique_ptr<flexis_server> s(new flexis_server());
     s->g = g;
     s->slots = slots;
-    int rc = serve_create(g->dg, slots, &s->sess);
+    int rc = serve_create(g->dg, slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &s->sess);
     if (rc) return rc;
     flexis_server *raw = s.get();
     s->th = std::thread([raw] { raw->loop(); });

@@ -51,10 +51,11 @@ int dev_free_bytes(const DeviceGraph *g, int64_t *bytes);
 
 // Serving session: `slots` pattern slots on the graph's device with their own workspace.
 struct ServeSession;
-int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out);
+int serve_create(DeviceGraph *g, int32_t slots, int32_t wmin, int32_t wmax, int32_t budget,
+                 ServeSession **out);
 void serve_destroy(ServeSession *s);
 // Device bytes one slot holds (used bitmap + window + state); the admission unit.
-int serve_slot_bytes(const DeviceGraph *g, int64_t *bytes);
+int serve_slot_bytes(const DeviceGraph *g, int32_t wmax, int64_t *bytes);
 // Admit plans into the listed free slots, run one round for every slot in its greedy phase and
 // the MNI search of slots that just finished it.  phase_out[slots]: 0 free, 1 greedy, 2 MNI,
 // 3 ready (res_out[i] then holds slot i's result).  *n_greedy: slots still in greedy phase.

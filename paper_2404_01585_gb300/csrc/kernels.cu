@@ -1534,12 +1534,21 @@ int dev_selected(DeviceGraph *g, int32_t i, int32_t *maps_out, int64_t cap, int6
 // one speculation round over every slot still in its greedy phase, runs the MNI search for the
 // slots that finished their greedy phase in that round, and returns every slot's phase and
 // result.  Requests admitted at different steps share the device rounds.
+constexpr int SERVE_WMAX = 2048;
+constexpr int SERVE_BUDGET = 256;
+
 struct ServeSession {
     DeviceGraph *g = nullptr;
     Workspace w;
     cudaStream_t stream = nullptr;
     int32_t slots = 0;
-    int Wmin = 32, Wmax = 2048;
+    // A request starts at a window of Wmin roots, doubling up to Wmax while its speculation
+    // stays conflict-free.  Rounds are shared by every request in flight, so a round lasts as
+    // long as its longest search: the per-round search budget is much smaller than a batch's
+    // (measured on the MiCo-shaped serving stream: 4096 -> 256 chunks cut p50 from 49 to 8 ms
+    // and p99 from 435 to 161 ms, and raised the saturated throughput 1.7x).
+    int Wmin = 32, Wmax = SERVE_WMAX;
+    int32_t budget = SERVE_BUDGET;
     int32_t *d_admit = nullptr;
     int32_t *h_admit = nullptr;  // pinned
     Plan *h_plans = nullptr;     // pinned staging
@@ -1549,11 +1558,15 @@ struct ServeSession {
     int sblocks = 0;
 };
 
-int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out) {
+int serve_create(DeviceGraph *g, int32_t slots, int32_t wmin, int32_t wmax, int32_t budget,
+                 ServeSession **out) {
     CK(cudaSetDevice(g->device));
     ServeSession *s = new ServeSession();
     s->g = g;
     s->slots = slots;
+    if (wmax > 0) s->Wmax = std::max(32, std::min(wmax, 16384));
+    if (wmin > 0) s->Wmin = std::max(1, std::min(wmin, s->Wmax));
+    if (budget != 0) s->budget = budget;
     int rc = ws_ensure(g, s->w, slots, s->Wmax, 0);
     if (rc) { serve_destroy(s); return rc; }
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1565,6 +1578,7 @@ int serve_create(DeviceGraph *g, int32_t slots, ServeSession **out) {
         serve_destroy(s);
         return FLEXIS_E_NOMEM;
     }
+    memset(s->h_st, 0, sizeof(PatState) * slots);  // host view: every slot free
     EvalConfig cfg;
     s->sblocks = search_grid(g, cfg);
     // every slot starts free
@@ -1590,8 +1604,8 @@ void serve_destroy(ServeSession *s) {
     delete s;
 }
 
-int serve_slot_bytes(const DeviceGraph *g, int64_t *bytes) {
-    const int64_t W = ServeSession().Wmax;
+int serve_slot_bytes(const DeviceGraph *g, int32_t wmax, int64_t *bytes) {
+    const int64_t W = wmax > 0 ? std::max(32, std::min(wmax, 16384)) : ServeSession().Wmax;
     *bytes = (int64_t)g->view.words * 4 + W * (2 * (4 + 4 + 4 * MAXN) + 8) + (int64_t)sizeof(PatState) +
              (int64_t)sizeof(Plan);
     return FLEXIS_OK;
@@ -1602,6 +1616,7 @@ int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_pl
     DeviceGraph *g = s->g;
     CK(cudaSetDevice(g->device));
     Batch B = make_batch(g, s->w, s->w.plans, s->slots, s->Wmin, s->Wmax, 0, s->w.results);
+    B.budget = s->budget < 0 ? 0u : (uint32_t)s->budget;
     for (int32_t i = 0; i < n_admit; i++) {
         s->h_admit[i] = admit_slots[i];
         s->h_plans[i] = admit_plans[i];
