@@ -374,7 +374,8 @@ def main():
                 "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                        "supports_per_step": total_c // args.steps}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(stats.get("kernel_launches", 0)), "clocks": clk,
+                "gpu_launches": int(stats.get("kernel_launches", 0)),
+                "graph_replays": int(stats.get("graph_launches", 0)), "clocks": clk,
                 "batched_vs_plain": bvp, "serving": serving,
                 "kernel_time_ms": {"search": stats["search_ms"], "device_total": stats["total_ms"],
                                    "host_candidate_generation": stats["host_gen_ms"],

@@ -87,7 +87,10 @@ typedef struct {
     int32_t split_pieces;    /* pieces a suspended search heading its slot is split into per round:
                                 0 = default, -1 = never split */
     int32_t sub_searches;    /* saved sub-searches a pattern may hold at once (1..32): 0 = default */
-    int32_t reserved[6];
+    int32_t timing;          /* 1: CUDA events around every search launch (stats.search_ms) */
+    int32_t graphs;          /* 0 = default (the round loop of each level is captured once into a
+                                CUDA graph and replayed), -1 = launch kernel by kernel */
+    int32_t reserved[4];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
@@ -156,7 +159,8 @@ typedef struct {
     float host_compile_ms;    /* host time in pattern compilation */
     int32_t search_launches;  /* launches of the greedy search kernel */
     int32_t batches;          /* device batches (memory-admitted chunks of the patterns) */
-    int32_t pad;
+    int32_t graph_launches;   /* replays of the captured round-loop CUDA graph (each runs the
+                                 rounds between two host checks); 0 when launched one by one */
 } flexis_stats;
 
 const char *flexis_status_string(int status);

@@ -46,7 +46,8 @@ class flexis_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("device", C.c_int32), ("window_min", C.c_int32),
                 ("window_max", C.c_int32), ("search_blocks", C.c_int32),
                 ("record_selected", C.c_int32), ("search_budget", C.c_int32),
-                ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("timing", C.c_int32),
+                ("graphs", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class flexis_pattern(C.Structure):
@@ -83,10 +84,10 @@ class flexis_stats(C.Structure):
                 ("alg_bytes_greedy", C.c_int64), ("patterns", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
                 ("total_ms", C.c_float), ("host_gen_ms", C.c_float), ("host_compile_ms", C.c_float),
-                ("search_launches", C.c_int32), ("batches", C.c_int32), ("pad", C.c_int32)]
+                ("search_launches", C.c_int32), ("batches", C.c_int32), ("graph_launches", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # symbol table: name -> (restype, argtypes); every symbol include/flexis.h declares
@@ -183,10 +184,7 @@ def default_options(**kw) -> flexis_options:
     o = flexis_options()
     lib().flexis_default_options(C.byref(o))
     for k, v in kw.items():
-        if k == "timing":
-            o.reserved[0] = 1 if v else 0
-        else:
-            setattr(o, k, v)
+        setattr(o, k, int(v))
     return o
 
 

@@ -76,6 +76,7 @@ void add_stats(flexis_stats &a, const flexis_stats &b) {
     a.host_compile_ms += b.host_compile_ms;
     a.search_launches += b.search_launches;
     a.batches += b.batches;
+    a.graph_launches += b.graph_launches;
 }
 
 // Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism
@@ -96,7 +97,8 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.search_blocks = g->opt.search_blocks;
     c.record_selected = g->opt.record_selected;
     c.rounds_per_sync = P >= 64 ? 4 : 2;
-    c.timing = g->opt.reserved[0] != 0;
+    c.timing = g->opt.timing != 0;
+    c.graphs = g->opt.graphs >= 0;
     c.search_budget = g->opt.search_budget != 0 ? g->opt.search_budget : P < SMALL_BATCH ? SMALL_BATCH_BUDGET : 0;
     c.split_pieces = g->opt.split_pieces;
     c.sub_searches = g->opt.sub_searches;

@@ -18,6 +18,7 @@ struct EvalConfig {
     int32_t split_pieces = 0;   // 0: default pieces per split; < 0: never split
     int32_t sub_searches = 0;   // 0: default saved sub-searches per pattern
     bool timing = false;        // per-launch CUDA events around the search kernel
+    bool graphs = true;         // replay the round loop as a captured CUDA graph (not with timing)
 };
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);

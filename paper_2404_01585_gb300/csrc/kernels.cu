@@ -1103,6 +1103,9 @@ struct DeviceGraph {
     int32_t last_P = 0, last_sel = 0;
     cudaEvent_t ev[2]{};
     std::vector<cudaEvent_t> sev;
+    cudaGraphExec_t round_exec = nullptr;  // the captured round loop of the last level
+    std::vector<cudaEvent_t> gev;          // search-launch events inside the captured graph
+    int64_t graph_instantiations = 0, graph_fallbacks = 0;
 };
 
 template <class T>
@@ -1217,6 +1220,8 @@ void dev_graph_destroy(DeviceGraph *g) {
     if (g->ev[0]) cudaEventDestroy(g->ev[0]);
     if (g->ev[1]) cudaEventDestroy(g->ev[1]);
     for (auto e : g->sev) cudaEventDestroy(e);
+    if (g->round_exec) cudaGraphExecDestroy(g->round_exec);
+    for (auto e : g->gev) cudaEventDestroy(e);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1264,6 +1269,54 @@ static int search_grid(const DeviceGraph *g, const EvalConfig &cfg) {
     return cfg.search_blocks > 0 ? cfg.search_blocks : g->sm_count * std::max(1, per_sm);
 }
 
+// Capture R rounds (commit + search, alternating window buffers from 0) and the control-word
+// read into g->round_exec, updating the executable graph in place when only the kernel
+// parameters changed.  Returns 0 on success; on any failure the stream is left out of capture,
+// the error is cleared, and the caller launches the kernels one by one.
+static int capture_rounds(DeviceGraph *g, const Batch &B, int R, int commit_blocks, size_t smem, int sblocks,
+                          cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl, const cudaEvent_t *tev) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    for (int r = 0; r < R; r++) {
+        k_commit<<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, r & 1);
+        // an event record node needs the external flag (a plain record inside a capture only
+        // orders streams)
+        if (tev) cudaEventRecordWithFlags(tev[2 * r], stream, cudaEventRecordExternal);
+        k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, r & 1);
+        if (tev) cudaEventRecordWithFlags(tev[2 * r + 1], stream, cudaEventRecordExternal);
+    }
+    cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
+    const cudaError_t ce = cudaStreamEndCapture(stream, &gr);
+    if (ce != cudaSuccess || gr == nullptr) {
+        if (gr) cudaGraphDestroy(gr);
+        (void)cudaGetLastError();
+        return 1;
+    }
+    bool ok = false;
+    if (g->round_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        ok = cudaGraphExecUpdate(g->round_exec, gr, &info) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(g->round_exec);
+            g->round_exec = nullptr;
+        }
+    }
+    if (!ok) {
+        ok = cudaGraphInstantiate(&g->round_exec, gr, 0) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            g->round_exec = nullptr;
+        }
+        g->graph_instantiations += ok;
+    }
+    cudaGraphDestroy(gr);
+    return ok ? 0 : 1;
+}
+
 int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_result *d_results,
              cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats) {
     if (P <= 0) return FLEXIS_OK;
@@ -1297,9 +1350,50 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     launches += 1;
     int64_t rounds = 0;
     int search_launches = 0;
-    const int R = std::max(1, cfg.rounds_per_sync);
+    int R = std::max(1, cfg.rounds_per_sync);
     size_t evi = 0;
-    for (;;) {
+    // The R rounds between two host checks (commit + search each, then the control-word read)
+    // are captured once per level into a CUDA graph and replayed: the round loop's launches
+    // cost one graph launch per R rounds.  R is even so that the window buffer parity of a
+    // replay matches the rounds it stands for.
+    // With timing, the graph also records an event pair around each search launch; the pairs
+    // are read after every replay.
+    const bool use_graph = cfg.graphs && stream != nullptr && stream != cudaStreamLegacy &&
+                           stream != cudaStreamPerThread;
+    bool graph_done = false;
+    int64_t graph_launches = 0;
+    float graph_search_ms = 0.f;
+    if (use_graph) {
+        R += R & 1;
+        while (cfg.timing && g->gev.size() < (size_t)(2 * R)) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            g->gev.push_back(e);
+        }
+        if (!capture_rounds(g, B, R, commit_blocks, smem, sblocks, stream, w.h_ctl, w.ctl,
+                            cfg.timing ? g->gev.data() : nullptr)) {
+            for (;;) {
+                CK(cudaGraphLaunch(g->round_exec, stream));
+                launches += 2 * R;
+                search_launches += R;
+                rounds += R;
+                CK(cudaStreamSynchronize(stream));
+                graph_launches++;
+                if (cfg.timing) {
+                    for (int r = 0; r < R; r++) {
+                        float x = 0.f;
+                        CK(cudaEventElapsedTime(&x, g->gev[2 * r], g->gev[2 * r + 1]));
+                        graph_search_ms += x;
+                    }
+                }
+                if (w.h_ctl->active[(rounds - 1) & 1] == 0) break;
+            }
+            graph_done = true;
+        } else {
+            g->graph_fallbacks++;
+        }
+    }
+    if (!graph_done) for (;;) {
         for (int r = 0; r < R; r++) {
             const int q = (int)(rounds & 1);
             k_commit<<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
@@ -1349,6 +1443,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
         stats->alg_bytes_greedy = (int64_t)w.h_ctl->bytes_greedy;
         stats->alg_bytes = (int64_t)(w.h_ctl->bytes_greedy + w.h_ctl->bytes_mni);
         stats->search_launches = search_launches;
+        stats->graph_launches = (int32_t)graph_launches;
         stats->d2h_bytes = (int64_t)sizeof(Ctl) * (rounds / R + 1);  // control-word reads
         float t = 0.f;
         cudaEventElapsedTime(&t, g->ev[0], g->ev[1]);
@@ -1360,7 +1455,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
                 cudaEventElapsedTime(&x, g->sev[k], g->sev[k + 1]);
                 sum += x;
             }
-            stats->search_ms = sum;
+            stats->search_ms = sum + graph_search_ms;
             float y = 0.f;
             cudaEventElapsedTime(&y, m0, m1);
             stats->mni_ms = y;

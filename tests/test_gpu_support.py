@@ -133,10 +133,12 @@ def test_plain_equals_batched_and_launch_shape_free(powerlaw):
     for opts in ({}, dict(window_min=1, window_max=32), dict(window_min=1024, window_max=1024),
                  dict(search_blocks=3), dict(window_min=7, window_max=64, search_blocks=151),
                  dict(search_budget=1), dict(search_budget=3, window_min=4096, window_max=16384),
-                 dict(search_budget=-1)):
+                 dict(search_budget=-1), dict(graphs=-1), dict(timing=1), dict(graphs=-1, timing=1)):
         g = fx.Graph(lab, src, dst, **opts)
         for mode in (EARLY, FULL):
             batch = [key(r) for r in g.support_batch(pats, 60, 0.5, mode)]
+            # the round loop is replayed as a captured CUDA graph unless turned off
+            assert (g.stats()["graph_launches"] > 0) == (opts.get("graphs", 0) >= 0), opts
             if ref is None:
                 ref = {}
             if mode not in ref:
