@@ -113,7 +113,7 @@ def load_inputs():
 
 
 def config_dict(extra=None):
-    d = {"workload": "MiCo-shaped mining sweep (configs[1]): Chung-Lu gamma=2.3, 100000 v, "
+    d = {"workload": "MiCo-shaped mining sweep: Chung-Lu gamma=2.3, 100000 v, "
                      "1080000 e, 29 labels Zipf(1.2); patterns up to 5 edges",
          "sweep_sigma_lambda": SWEEP, "max_edges": MAX_EDGES, "mode": "EARLY (stop at tau), mIS decision",
          "l2": "flushed between steps (256 MiB device write)", "graph_seed": 1002}
