@@ -90,7 +90,16 @@ typedef struct {
     int32_t timing;          /* 1: CUDA events around every search launch (stats.search_ms) */
     int32_t graphs;          /* 0 = default (the round loop of each level is captured once into a
                                 CUDA graph and replayed), -1 = launch kernel by kernel */
-    int32_t reserved[4];
+    int32_t deadline_ms;     /* > 0: wall-clock limit of one evaluation call (support, batch, each
+                                device batch of a mining level) and of one served request (from
+                                its submission).  Patterns still undecided when it passes stop
+                                between two rounds and report status FLEXIS_E_TIMEOUT, with mis =
+                                the maps committed so far (a lower bound of their mIS), mni = -1
+                                and frequent = 0 (undecided); flexis_mine then fails with
+                                FLEXIS_E_TIMEOUT.  The limit is checked between rounds of the
+                                greedy phase; the MNI pass of FLEXIS_MODE_FULL is not bounded by
+                                it.  0 = no limit (default). */
+    int32_t reserved[3];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

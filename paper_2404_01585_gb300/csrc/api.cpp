@@ -99,6 +99,7 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.rounds_per_sync = P >= 64 ? 4 : 2;
     c.timing = g->opt.timing != 0;
     c.graphs = g->opt.graphs >= 0;
+    c.deadline_ms = g->opt.deadline_ms;
     c.search_budget = g->opt.search_budget != 0 ? g->opt.search_budget : P < SMALL_BATCH ? SMALL_BATCH_BUDGET : 0;
     c.split_pieces = g->opt.split_pieces;
     c.sub_searches = g->opt.sub_searches;
@@ -334,6 +335,11 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
         int rc = eval_plans(g, plans, res.data());
         if (rc) return rc;
         add_stats(total, g->last);
+        for (size_t i = 0; i < C.size(); i++)
+            if (res[i].status == FLEXIS_E_TIMEOUT) {
+                g->last = total;
+                return FLEXIS_E_TIMEOUT;  // a level with undecided patterns has no frequent set
+            }
         std::vector<Code> F;
         for (size_t i = 0; i < C.size(); i++)
             if (res[i].status == FLEXIS_OK && res[i].frequent) {
@@ -488,6 +494,7 @@ struct flexis_server {
     flexis_graph *g = nullptr;
     ServeSession *sess = nullptr;
     int32_t slots = 0;
+    int32_t deadline_ms = 0;  // per request, from submission; 0 = none
     std::thread th;
     std::mutex mu;
     std::condition_variable cv;
@@ -500,7 +507,7 @@ struct flexis_server {
     void loop() {
         std::vector<int64_t> slot_id((size_t)slots, -1);
         std::vector<clock::time_point> slot_t0((size_t)slots);
-        std::vector<int32_t> phase((size_t)slots, 0), admit;
+        std::vector<int32_t> phase((size_t)slots, 0), admit, cancel;
         std::vector<Plan> aplans;
         std::vector<flexis_support_result> res((size_t)slots);
         int busy = 0;
@@ -534,6 +541,21 @@ struct flexis_server {
                 break;
             }
             auto now = clock::now();
+            // requests past their deadline stop before the next step, which reports them
+            cancel.clear();
+            if (deadline_ms > 0) {
+                for (int32_t i = 0; i < slots; i++) {
+                    if (slot_id[(size_t)i] < 0 || phase[(size_t)i] == 3) continue;
+                    if (std::chrono::duration<double, std::milli>(now - slot_t0[(size_t)i]).count() > deadline_ms)
+                        cancel.push_back(i);
+                }
+            }
+            if (!cancel.empty() && (rc = serve_cancel(sess, cancel.data(), (int32_t)cancel.size())) != 0) {
+                std::lock_guard<std::mutex> lk(mu);
+                err = rc;
+                stop = true;
+                break;
+            }
             std::lock_guard<std::mutex> lk(mu);
             for (int32_t i = 0; i < slots; i++) {
                 if (slot_id[(size_t)i] < 0 || phase[(size_t)i] != 3) continue;
@@ -562,6 +584,7 @@ int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out) {
     std::unique_ptr<flexis_server> s(new flexis_server());
     s->g = g;
     s->slots = slots;
+    s->deadline_ms = g->opt.deadline_ms;
     int rc = serve_create(g->dg, slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &s->sess);
     if (rc) return rc;
     flexis_server *raw = s.get();

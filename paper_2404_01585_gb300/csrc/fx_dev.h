@@ -18,7 +18,8 @@ struct EvalConfig {
     int32_t split_pieces = 0;   // 0: default pieces per split; < 0: never split
     int32_t sub_searches = 0;   // 0: default saved sub-searches per pattern
     bool timing = false;        // per-launch CUDA events around the search kernel
-    bool graphs = true;         // replay the round loop as a captured CUDA graph (not with timing)
+    bool graphs = true;         // replay the round loop as a captured CUDA graph
+    int32_t deadline_ms = 0;    // > 0: patterns undecided after this long stop with FLEXIS_E_TIMEOUT
 };
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);
@@ -60,6 +61,7 @@ int serve_slot_bytes(const DeviceGraph *g, int32_t wmax, int64_t *bytes);
 // Admit plans into the listed free slots, run one round for every slot in its greedy phase and
 // the MNI search of slots that just finished it.  phase_out[slots]: 0 free, 1 greedy, 2 MNI,
 // 3 ready (res_out[i] then holds slot i's result).  *n_greedy: slots still in greedy phase.
+int serve_cancel(ServeSession *s, const int32_t *slots, int32_t n);
 int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_plans, int32_t n_admit,
                int32_t *phase_out, flexis_support_result *res_out, int32_t *n_greedy);
 

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -78,7 +79,7 @@ struct PatState {
     uint32_t max_steps;        // largest chunk count of one greedy search
     int32_t buf;               // current window buffer (0 or 1)
     uint32_t susp_mask;        // saved-search slots in use (KSUSP bits)
-    uint32_t pad3;
+    uint32_t cancelled;        // stopped at a deadline before its decision
 };
 
 struct Ctl {
@@ -946,7 +947,7 @@ __global__ void k_mni_setup(Batch B) {
             const int p = sidx / MAXN, o = sidx % MAXN;
             const Plan &P = B.plans[p];
             const PatState &S = B.st[p];
-            const bool need = S.phase == PH_MNI && P.status == FLEXIS_OK && P.want_mni &&
+            const bool need = S.phase == PH_MNI && !S.cancelled && P.status == FLEXIS_OK && P.want_mni &&
                               !(P.flags & FLEXIS_FLAG_ABSENT_LABEL) && S.count < P.cap && S.count > 0;
             if (need && o < P.n_orb) {
                 const int u = P.orb[o].vert[0];
@@ -1016,6 +1017,20 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
     }
 }
 
+// Deadline: patterns still in their greedy phase stop between two rounds (no search is in
+// flight then) and are finalised with FLEXIS_E_TIMEOUT.  `slots` (nullable) lists the patterns
+// to stop; NULL stops every pattern of the batch.
+__global__ void k_cancel(Batch B, const int32_t *slots, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = slots ? slots[i] : i;
+    PatState &S = B.st[p];
+    if (S.phase != PH_GREEDY) return;
+    S.cancelled = 1;
+    S.done = 1;
+    S.phase = PH_MNI;
+}
+
 __global__ void k_finalize(Batch B) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= B.P) return;
@@ -1057,6 +1072,13 @@ __global__ void k_finalize(Batch B) {
         r.mni = mni;
         const int64_t c = P.tau > 1 ? P.tau : 1;
         r.frequent = mis >= c ? 1 : 0;
+        if (S.cancelled) {
+            // stopped before its decision: mis counts the maps committed so far (a lower bound
+            // of the pattern's mIS); nothing is decided
+            r.status = FLEXIS_E_TIMEOUT;
+            r.mni = -1;
+            r.frequent = 0;
+        }
     }
     B.results[p] = r;
 }
@@ -1320,6 +1342,7 @@ static int capture_rounds(DeviceGraph *g, const Batch &B, int R, int commit_bloc
 int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_result *d_results,
              cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats) {
     if (P <= 0) return FLEXIS_OK;
+    const auto t_start = std::chrono::steady_clock::now();
     CK(cudaSetDevice(g->device));
     const int Wmax = std::max(32, std::min(cfg.w_max, 16384));
     const int Wmin = std::max(1, std::min(cfg.w_min, Wmax));
@@ -1363,6 +1386,14 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     bool graph_done = false;
     int64_t graph_launches = 0;
     float graph_search_ms = 0.f;
+    // the deadline is checked where the host waits anyway (between groups of rounds)
+    bool timed_out = false;
+    auto past_deadline = [&]() {
+        if (cfg.deadline_ms <= 0) return false;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        timed_out = ms > cfg.deadline_ms;
+        return timed_out;
+    };
     if (use_graph) {
         R += R & 1;
         while (cfg.timing && g->gev.size() < (size_t)(2 * R)) {
@@ -1387,6 +1418,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
                     }
                 }
                 if (w.h_ctl->active[(rounds - 1) & 1] == 0) break;
+                if (past_deadline()) break;
             }
             graph_done = true;
         } else {
@@ -1418,6 +1450,11 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
         CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         if (w.h_ctl->active[(rounds - 1) & 1] == 0) break;
+        if (past_deadline()) break;
+    }
+    if (timed_out) {
+        k_cancel<<<(P + 255) / 256, 256, 0, stream>>>(B, nullptr, P);
+        launches += 1;
     }
     cudaEvent_t m0 = nullptr, m1 = nullptr;
     if (cfg.timing) {
@@ -1646,6 +1683,8 @@ struct ServeSession {
     int32_t budget = SERVE_BUDGET;
     int32_t *d_admit = nullptr;
     int32_t *h_admit = nullptr;  // pinned
+    int32_t *d_cancel = nullptr;
+    int32_t *h_cancel = nullptr;  // pinned
     Plan *h_plans = nullptr;     // pinned staging
     PatState *h_st = nullptr;    // pinned
     flexis_support_result *h_res = nullptr;  // pinned
@@ -1667,6 +1706,8 @@ int serve_create(DeviceGraph *g, int32_t slots, int32_t wmin, int32_t wmax, int3
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&s->d_admit, sizeof(int32_t) * slots) != cudaSuccess ||
         cudaMallocHost((void **)&s->h_admit, sizeof(int32_t) * slots) != cudaSuccess ||
+        cudaMalloc(&s->d_cancel, sizeof(int32_t) * slots) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_cancel, sizeof(int32_t) * slots) != cudaSuccess ||
         cudaMallocHost((void **)&s->h_plans, sizeof(Plan) * slots) != cudaSuccess ||
         cudaMallocHost((void **)&s->h_st, sizeof(PatState) * slots) != cudaSuccess ||
         cudaMallocHost((void **)&s->h_res, sizeof(flexis_support_result) * slots) != cudaSuccess) {
@@ -1692,6 +1733,8 @@ void serve_destroy(ServeSession *s) {
     ws_free(s->w);
     cudaFree(s->d_admit);
     if (s->h_admit) cudaFreeHost(s->h_admit);
+    cudaFree(s->d_cancel);
+    if (s->h_cancel) cudaFreeHost(s->h_cancel);
     if (s->h_plans) cudaFreeHost(s->h_plans);
     if (s->h_st) cudaFreeHost(s->h_st);
     if (s->h_res) cudaFreeHost(s->h_res);
@@ -1703,6 +1746,20 @@ int serve_slot_bytes(const DeviceGraph *g, int32_t wmax, int64_t *bytes) {
     const int64_t W = wmax > 0 ? std::max(32, std::min(wmax, 16384)) : ServeSession().Wmax;
     *bytes = (int64_t)g->view.words * 4 + W * (2 * (4 + 4 + 4 * MAXN) + 8) + (int64_t)sizeof(PatState) +
              (int64_t)sizeof(Plan);
+    return FLEXIS_OK;
+}
+
+// Stop the listed requests before the next step (their deadline passed); that step finalises
+// them with FLEXIS_E_TIMEOUT.
+int serve_cancel(ServeSession *s, const int32_t *slots, int32_t n) {
+    if (n <= 0) return FLEXIS_OK;
+    DeviceGraph *g = s->g;
+    CK(cudaSetDevice(g->device));
+    memcpy(s->h_cancel, slots, sizeof(int32_t) * (size_t)n);
+    CK(cudaMemcpyAsync(s->d_cancel, s->h_cancel, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s->stream));
+    Batch B = make_batch(g, s->w, s->w.plans, s->slots, s->Wmin, s->Wmax, 0, s->w.results);
+    k_cancel<<<(n + 255) / 256, 256, 0, s->stream>>>(B, s->d_cancel, n);
+    CK(cudaGetLastError());
     return FLEXIS_OK;
 }
 

@@ -6,6 +6,7 @@ from __future__ import annotations
 
 import json
 import os
+import time
 
 import numpy as np
 import pytest
@@ -241,6 +242,46 @@ def test_serving_alone_equals_mixed(powerlaw):
         time.sleep(0.001)
     srv.stop()
     assert [key(got[i]) for i in range(len(pats))] == alone
+    g.close()
+
+
+def test_deadline_stops_undecided_patterns_only(powerlaw):
+    # one-root windows make every pattern take a round per root, so a 1 ms limit passes while
+    # many patterns are undecided; the decided ones keep their exact values
+    lab, src, dst, pats = powerlaw
+    g0 = fx.Graph(lab, src, dst)
+    ref = g0.support_batch(pats, 60, 0.5, EARLY)
+    g0.close()
+    g = fx.Graph(lab, src, dst, window_min=1, window_max=32, deadline_ms=1)
+    res = g.support_batch(pats, 60, 0.5, EARLY)
+    stopped = 0
+    for r, w in zip(res, ref):
+        if r["status"] == fx.FLEXIS_E_TIMEOUT:
+            stopped += 1
+            assert 0 <= r["mis"] <= w["mis"] and r["mni"] == -1 and not r["frequent"]
+        else:
+            assert r["status"] == 0 and key(r) == key(w)
+    assert 0 < stopped < len(pats)
+    with pytest.raises(fx.FlexisError) as e:
+        g.mine(30, 0.5, 4)
+    assert e.value.code == fx.FLEXIS_E_TIMEOUT
+    # served requests: the limit runs from submission
+    srv = fx.Server(g, slots=8)
+    for i, (pl, pe) in enumerate(pats[:24]):
+        assert srv.submit(i, pl, pe, 60, 0.5) == 0
+    got, t0 = {}, time.time()
+    while len(got) < 24 and time.time() - t0 < 120:
+        for rid, r, lat in srv.poll():
+            got[rid] = r
+        time.sleep(0.001)
+    srv.stop()
+    assert len(got) == 24
+    for i in range(24):
+        r = got[i]
+        assert r["status"] in (0, fx.FLEXIS_E_TIMEOUT)
+        if r["status"] == 0:
+            assert key(r) == key(ref[i])
+    assert any(got[i]["status"] == fx.FLEXIS_E_TIMEOUT for i in range(24))
     g.close()
 
 
