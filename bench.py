@@ -139,50 +139,67 @@ def run_oracle_sample(lab, src, dst):
     return cand, dt, desc
 
 
-def serving_leg(g, fx, lab, nq=300, rates=(0.3, 0.6, 0.9), seed=2005):
-    """Continuous-batching serving on the resident graph: a Poisson stream of support queries
-    (pattern of 3-8 vertices: random tree / cycle / clique with labels from the graph's label
-    distribution; sigma in {1000, 5000, 20000}; lambda in {0, 0.5, 1}; EARLY, mIS decision) at
-    three arrival rates, each a fraction of the saturated batch throughput of the same queries.
-    Latency = submit -> result, measured by the server."""
+SERVE_SLOTS = 256
+
+
+def serving_leg(g, fx, lab, nq=2000, rates=(0.3, 0.6, 0.9), seed=2005, per_rate_s=20.0, graph_name=""):
+    """Continuous-batching serving on a resident graph.  Queries: pattern of 3-8 vertices (random
+    tree / cycle / clique, labels drawn from the graph's label distribution), sigma in
+    {1000, 5000, 20000}, lambda in {0, 0.5, 1}, EARLY mIS decision; each request has the graph's
+    deadline (options.deadline_ms, from submission) and reports FLEXIS_E_TIMEOUT past it.
+    Saturated throughput: the `nq` queries in a closed loop (SERVE_SLOTS requests outstanding),
+    decided requests / elapsed time.  Then a Poisson stream at each fraction of that rate, about
+    `per_rate_s` seconds of arrivals.  Latency = submit -> result, measured by the server."""
     from workloads import Stream, random_patterns
     pats = random_patterns(nq, range(3, 9), ["tree", "cycle", "clique"], lab, seed)
     st = Stream(seed + 1)
     sig = [int((1000, 5000, 20000)[int(x)]) for x in st.integers(nq, 3)]
     lam = [float((0.0, 0.5, 1.0)[int(x)]) for x in st.integers(nq, 3)]
     mode = fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI
-    t0 = time.perf_counter()
-    g.support_batch(pats, sig, lam, mode)
-    sat = nq / (time.perf_counter() - t0)
-    out = {"queries_per_rate": nq, "saturated_batch_qps": sat,
-           "workload": "Poisson stream, patterns 3-8 vertices (tree/cycle/clique), "
-                       "sigma {1000,5000,20000} x lambda {0,0.5,1}, EARLY mIS decision", "rates": []}
-    for frac in rates:
-        rate = frac * sat
-        nr = min(nq, max(60, int(20 * rate)))  # about 20 s of arrivals per rate at most
-        gaps = -np.log(1.0 - st.uniform(nr)) / rate
-        srv = fx.Server(g, slots=256)
-        lat, done = {}, 0
+
+    def run(order, due):
+        srv = fx.Server(g, slots=SERVE_SLOTS)
+        got = {}
         start = time.perf_counter()
-        due = start + np.cumsum(gaps)
-        for i in range(nr):
-            while time.perf_counter() < due[i]:
+        for k, i in enumerate(order):
+            # open loop: wait for the arrival time; closed loop (due None): keep SERVE_SLOTS
+            # requests outstanding
+            while (time.perf_counter() < start + due[k]) if due is not None else (k - len(got) >= SERVE_SLOTS):
                 for rid, r, us in srv.poll():
-                    lat[rid] = us
+                    got[rid] = (r["status"], us)
                 time.sleep(0.0002)
-            while srv.submit(i, pats[i][0], pats[i][1], sig[i], lam[i], mode) == fx.FLEXIS_E_BUSY:
+            while srv.submit(k, pats[i][0], pats[i][1], sig[i], lam[i], mode) == fx.FLEXIS_E_BUSY:
                 time.sleep(0.001)
-        while len(lat) < nr and time.perf_counter() - start < 180:
+        while len(got) < len(order) and time.perf_counter() - start < 600:
             for rid, r, us in srv.poll():
-                lat[rid] = us
+                got[rid] = (r["status"], us)
             time.sleep(0.0005)
         end = time.perf_counter()
         srv.stop()
-        L = sorted(lat.values())
-        out["rates"].append({"arrival_fraction_of_saturated": frac, "offered_qps": rate,
-                             "submitted": nr, "completed": len(L), "achieved_qps": len(L) / (end - start),
-                             "p50_ms": L[len(L) // 2] / 1e3 if L else None,
-                             "p99_ms": L[min(len(L) - 1, int(len(L) * 0.99))] / 1e3 if L else None})
+        ok = sorted(us / 1e3 for stt, us in got.values() if stt == 0)
+        allv = sorted(us / 1e3 for stt, us in got.values())
+
+        def pct(v, q):
+            return v[min(len(v) - 1, int(len(v) * q))] if v else None
+        return {"submitted": len(order), "decided": len(ok),
+                "timed_out": sum(1 for stt, _ in got.values() if stt == fx.FLEXIS_E_TIMEOUT),
+                "elapsed_s": end - start, "decided_qps": len(ok) / (end - start),
+                "p50_ms": pct(allv, 0.5), "p99_ms": pct(allv, 0.99),
+                "p50_ms_decided": pct(ok, 0.5), "p99_ms_decided": pct(ok, 0.99)}
+
+    sat = run(list(range(nq)), None)
+    rate_sat = max(sat["decided_qps"], 1.0)
+    out = {"graph": graph_name, "deadline_ms": int(g.options.deadline_ms), "saturated": sat,
+           "workload": "patterns 3-8 vertices (tree/cycle/clique), sigma {1000,5000,20000} x "
+                       "lambda {0,0.5,1}, EARLY mIS decision; Poisson arrivals", "rates": []}
+    for frac in rates:
+        rate = frac * rate_sat
+        nr = max(60, int(per_rate_s * rate))
+        order = [int(x) for x in st.integers(nr, nq)]
+        due = np.cumsum(-np.log(1.0 - st.uniform(nr)) / rate)
+        r = run(order, due)
+        r.update({"arrival_fraction_of_saturated": frac, "offered_qps": rate})
+        out["rates"].append(r)
     return out
 
 
