@@ -388,7 +388,8 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
     std::vector<std::vector<Code>> part((size_t)std::max(1, threads));
     std::atomic<size_t> next{0};
     auto work = [&](int tid) {
-        std::unordered_set<Code, CodeHash> local;
+        std::vector<Code> &local = part[(size_t)tid];
+        size_t limit = (size_t)1 << 22;
         for (;;) {
             size_t gi = next.fetch_add(1);
             if (gi >= groups.size()) break;
@@ -425,18 +426,23 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
                             if (mb >> i & 1) P.adj[i] |= (uint8_t)(1 << y);
                         }
                         if (!connected(P)) continue;
-                        local.insert(canonical(P, nullptr));
+                        local.push_back(canonical(P, nullptr));
                     }
+            if (local.size() > limit) {  // bound the repeats held
+                std::sort(local.begin(), local.end());
+                local.erase(std::unique(local.begin(), local.end()), local.end());
+                limit = std::max(limit, 2 * local.size());
+            }
         }
-        part[(size_t)tid].assign(local.begin(), local.end());
+        std::sort(local.begin(), local.end());
+        local.erase(std::unique(local.begin(), local.end()), local.end());
     };
     int T = std::max(1, threads);
     std::vector<std::thread> th;
     for (int t = 1; t < T; t++) th.emplace_back(work, t);
     work(0);
     for (auto &t : th) t.join();
-    std::unordered_set<Code, CodeHash> all;
-    for (auto &v : part) all.insert(v.begin(), v.end());
+    std::vector<Code> cliques;
     // cliques (Algorithm 4 + post-check): a k-clique whose every (k-1)-sub-clique is frequent
     for (const Code &c : F) {
         Pat Q = pat_of_code(c);
@@ -464,11 +470,30 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
                 for (int i = 0; i < R.n; i++) R.adj[i] = (uint8_t)(((1 << R.n) - 1) & ~(1 << i));
                 if (!Fset.count(canonical(R, nullptr))) ok = false;
             }
-            if (ok) all.insert(canonical(P, nullptr));
+            if (ok) cliques.push_back(canonical(P, nullptr));
         }
     }
-    out.assign(all.begin(), all.end());
-    std::sort(out.begin(), out.end());
+    std::sort(cliques.begin(), cliques.end());
+    part.push_back(std::move(cliques));
+    // union of the sorted runs (one per thread, plus the cliques): a k-way merge that drops
+    // repeats, so the output comes out sorted and unique
+    size_t total = 0;
+    for (auto &v : part) total += v.size();
+    out.reserve(total);
+    std::vector<size_t> at(part.size(), 0);
+    auto run_less = [&](size_t a, size_t b) { return part[b][at[b]] < part[a][at[a]]; };  // min-heap
+    std::vector<size_t> heap;
+    for (size_t r = 0; r < part.size(); r++)
+        if (!part[r].empty()) heap.push_back(r);
+    std::make_heap(heap.begin(), heap.end(), run_less);
+    while (!heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), run_less);
+        const size_t r = heap.back();
+        const Code &c = part[r][at[r]];
+        if (out.empty() || !(out.back() == c)) out.push_back(c);
+        if (++at[r] < part[r].size()) std::push_heap(heap.begin(), heap.end(), run_less);
+        else heap.pop_back();
+    }
 }
 
 }  // namespace fx
