@@ -3,7 +3,8 @@
 
 Workload (one step): the MiCo-shaped mining sweep -- a seeded Chung-Lu graph (exponent 2.3,
 100,000 vertices, 1,080,000 undirected edges, 29 vertex labels Zipf(1.2)); Algorithm 1 mining of
-all connected patterns with up to 5 edges, once per (sigma, lambda) of the sweep.  Every
+all connected patterns with up to 5 edges, once per (sigma, lambda) in {1000, 2000, 3000} x
+{0, 0.5, 1}.  Every
 candidate the mining loop evaluates (all levels, all runs) counts as one support evaluation.
 
   value : supports/s through flexis_mine with the graph already resident on the device
@@ -15,6 +16,9 @@ candidate the mining loop evaluates (all levels, all runs) counts as one support
           kernel itself / its summed CUDA-event time, against the measured HBM copy bandwidth.
   cpu_baseline : the plain C oracle, single thread, on a bounded sample of the same workload.
   batched_vs_plain : 256 candidates of the sweep evaluated in one batch vs one call each.
+  serving : continuous batching on the YouTube-shaped resident graph (Chung-Lu 2.3, 4.6 M
+          vertices, 43.9 M edges, 80 labels Zipf(1.0)): closed-loop saturated throughput, then
+          Poisson arrivals at 0.3 / 0.6 / 0.9 of it; p50 / p99 latency, 1 s request deadline.
 
 `python bench.py --impl reference` times the oracle instead (the reference arm of this build is
 its CPU oracle).  N > 1 (torchrun): independent replicas, one per GPU (the evaluation path has no
@@ -36,7 +40,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SWEEP = [(1000, 0.5), (2000, 0.5), (3000, 0.5), (1000, 1.0), (2000, 1.0), (3000, 1.0)]
+SWEEP = [(sigma, lam) for lam in (0.0, 0.5, 1.0) for sigma in (1000, 2000, 3000)]
 MAX_EDGES = 5
 METRIC = "candidate supports evaluated/sec (bit-exact vs oracle), batched vs plain on 1 GB300; p50/p99"
 UNIT = "supports/s"
@@ -140,6 +144,7 @@ def run_oracle_sample(lab, src, dst):
 
 
 SERVE_SLOTS = 256
+SERVE_DEADLINE_MS = 1000
 
 
 def serving_leg(g, fx, lab, nq=2000, rates=(0.3, 0.6, 0.9), seed=2005, per_rate_s=20.0, graph_name=""):
@@ -230,7 +235,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -376,7 +381,16 @@ def main():
            "plain_supports_per_s": len(sample) / sum(lat),
            "plain_p50_ms": 1e3 * lat[len(lat) // 2], "plain_p99_ms": 1e3 * lat[min(len(lat) - 1, int(len(lat) * 0.99))]}
 
-    serving = serving_leg(g, fx, lab) if rank == 0 and not args.skip_extras else None
+    serving = None
+    if rank == 0 and not args.skip_extras:
+        from workloads import make_graph
+        ylab, ysrc, ydst = make_graph("youtube")
+        gy = fx.Graph(ylab, ysrc, ydst, device=local, deadline_ms=SERVE_DEADLINE_MS)
+        serving = serving_leg(gy, fx, ylab, nq=1000, per_rate_s=15.0,
+                              graph_name="YouTube-shaped: Chung-Lu gamma=2.3, 4600000 v, 43900000 e, "
+                                         "80 labels Zipf(1.0)")
+        gy.close()
+        del ylab, ysrc, ydst
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
