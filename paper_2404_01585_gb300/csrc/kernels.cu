@@ -80,6 +80,7 @@ struct PatState {
     int32_t buf;               // current window buffer (0 or 1)
     uint32_t susp_mask;        // saved-search slots in use (KSUSP bits)
     uint32_t cancelled;        // stopped at a deadline before its decision
+    int32_t ndirty;            // used-bitmap words this pattern made non-zero (listed up to DIRTY_CAP)
 };
 
 struct Ctl {
@@ -109,6 +110,7 @@ struct Batch {
     uint32_t sid_all;     // saved sub-search indices a pattern may use (bit set)
     PatState *st;
     uint32_t *used;       // [P][words]
+    int32_t *dirty;       // [P][DIRTY_CAP] words of `used` made non-zero (nullable: not tracked)
     int32_t *win_root;    // [P][2][Wmax]  two window buffers per pattern
     int32_t *win_state;   // [P][2][Wmax]
     int32_t *win_map;     // [P][2][Wmax][8] (by level)
@@ -387,6 +389,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 
 // ------------------------------------------------------------------ kernels
 constexpr int SEARCH_THREADS = 256;
+constexpr int DIRTY_CAP = 1024;  // listed used-bitmap words per pattern (4 KB)
 constexpr int COMMIT_THREADS = 256;
 
 __device__ void reset_ctl(Ctl *c) {
@@ -776,7 +779,14 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         const int tot = block_scan(isc, excl, sh_scan);
         if (isc) {
             const int32_t *m = mp_cur + (size_t)s * MAXN;
-            for (int l = 0; l < n; l++) atomicOr(used + (m[l] >> 5), 1u << (m[l] & 31));
+            for (int l = 0; l < n; l++) {
+                const uint32_t wi = (uint32_t)m[l] >> 5;
+                const uint32_t old = atomicOr(used + wi, 1u << (m[l] & 31));
+                if (old == 0 && B.dirty) {  // first bit of this word: list it for the clean-up
+                    const int k = atomicAdd(&S->ndirty, 1);
+                    if (k < DIRTY_CAP) B.dirty[(size_t)p * DIRTY_CAP + k] = (int32_t)wi;
+                }
+            }
             const int64_t at = count0 + ncommit + excl;
             if (B.sel && at < B.sel_cap && at < P.cap) {
                 int32_t *o = B.sel + ((size_t)p * B.sel_cap + at) * MAXN;
@@ -1031,6 +1041,23 @@ __global__ void k_cancel(Batch B, const int32_t *slots, int n) {
     S.phase = PH_MNI;
 }
 
+// Leave every used bitmap of the batch zero again: a pattern that listed all the words it made
+// non-zero clears those, one that overflowed its list clears its whole bitmap.  One warp per
+// pattern.  The next evaluation then starts without clearing |V|/8 bytes per pattern.
+__global__ void k_clear_used(Batch B) {
+    const int p = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= B.P) return;
+    uint32_t *u = B.used + (size_t)p * B.G.words;
+    const int nd = B.st[p].ndirty;
+    if (nd <= DIRTY_CAP) {
+        const int32_t *d = B.dirty + (size_t)p * DIRTY_CAP;
+        for (int i = lane; i < nd; i += 32) u[d[i]] = 0u;
+    } else {
+        for (uint32_t w = lane; w < B.G.words; w += 32) u[w] = 0u;
+    }
+}
+
 __global__ void k_finalize(Batch B) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= B.P) return;
@@ -1101,6 +1128,8 @@ struct Workspace {
     int64_t bytes = 0;       // device bytes held
     PatState *st = nullptr;
     uint32_t *used = nullptr;
+    int32_t *dirty = nullptr;
+    int32_t clean = 0;  // patterns [0, clean) have all-zero used bitmaps between evaluations
     int32_t *win_root = nullptr, *win_state = nullptr, *win_map = nullptr;
     int2 *items = nullptr;
     Ctl *ctl = nullptr;
@@ -1142,7 +1171,7 @@ static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &by
 static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
 
 int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes) {
-    *bytes = (int64_t)g->view.words * 4 + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) + 8 * KSUSP +
+    *bytes = (int64_t)g->view.words * 4 + 4ll * DIRTY_CAP + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) + 8 * KSUSP +
              (int64_t)sizeof(PatState) + (int64_t)sizeof(Plan) + (int64_t)sizeof(flexis_support_result) +
              8 * (MAXN + 1) + (int64_t)sel * 4 * MAXN + 4ll * KSUSP * DFS_SAVE_STRIDE;
     return FLEXIS_OK;
@@ -1188,7 +1217,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
 }
 
 static void ws_free(Workspace &w) {
-    cudaFree(w.st); cudaFree(w.used); cudaFree(w.win_root); cudaFree(w.win_state);
+    cudaFree(w.st); cudaFree(w.used); cudaFree(w.dirty); cudaFree(w.win_root); cudaFree(w.win_state);
     cudaFree(w.win_map); cudaFree(w.items); cudaFree(w.ctl); cudaFree(w.sel_buf);
     cudaFree(w.mni_seg); cudaFree(w.plans); cudaFree(w.results); cudaFree(w.susp); cudaFree(w.alist);
     if (w.h_ctl) cudaFreeHost(w.h_ctl);
@@ -1214,6 +1243,8 @@ static int ws_ensure(const DeviceGraph *g, Workspace &w, int32_t P, int32_t Wmax
     CK(alloc((void **)&w.st, sizeof(PatState) * nP));
     CK(cudaMemset(w.st, 0, sizeof(PatState) * nP));
     CK(alloc((void **)&w.used, sizeof(uint32_t) * words * nP));
+    CK(alloc((void **)&w.dirty, sizeof(int32_t) * (size_t)DIRTY_CAP * nP));
+    w.clean = 0;
     CK(alloc((void **)&w.win_root, sizeof(int32_t) * (size_t)nSlots * 2));
     CK(alloc((void **)&w.win_state, sizeof(int32_t) * (size_t)nSlots * 2));
     CK(alloc((void **)&w.win_map, sizeof(int32_t) * (size_t)nSlots * 2 * MAXN));
@@ -1271,6 +1302,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
     B.sid_all = KSUSP >= 32 ? 0xFFFFFFFFu : ((1u << (KSUSP & 31)) - 1u);
     B.st = w.st;
     B.used = w.used;
+    B.dirty = w.dirty;
     B.win_root = w.win_root;
     B.win_state = w.win_state;
     B.win_map = w.win_map;
@@ -1367,7 +1399,13 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
 
     int64_t launches = 0;
     CK(cudaEventRecord(g->ev[0], stream));
-    CK(cudaMemsetAsync(w.used, 0, sizeof(uint32_t) * (size_t)g->view.words * P, stream));
+    // used bitmaps: only those not known to be zero are cleared here (the previous evaluation
+    // cleaned up after itself); until this one cleans up, none is known to be zero
+    const int32_t clean0 = w.clean;
+    w.clean = 0;
+    if (clean0 < P)
+        CK(cudaMemsetAsync(w.used + (size_t)g->view.words * clean0, 0,
+                           sizeof(uint32_t) * (size_t)g->view.words * (P - clean0), stream));
     CK(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), stream));
     k_init<<<(P + 255) / 256, 256, 0, stream>>>(B);
     launches += 1;
@@ -1466,8 +1504,10 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     k_mni<<<sblocks, SEARCH_THREADS, 0, stream>>>(B);
     if (cfg.timing) CK(cudaEventRecord(m1, stream));
     k_finalize<<<(P + 255) / 256, 256, 0, stream>>>(B);
-    launches += 3;
+    k_clear_used<<<(int)(((int64_t)P * 32 + 255) / 256), 256, 0, stream>>>(B);
+    launches += 4;
     CK(cudaGetLastError());
+    w.clean = std::max(clean0, P);
     CK(cudaEventRecord(g->ev[1], stream));
     CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));

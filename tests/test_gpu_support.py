@@ -285,6 +285,31 @@ def test_deadline_stops_undecided_patterns_only(powerlaw):
     g.close()
 
 
+def test_used_bitmaps_left_clean_between_calls():
+    # each evaluation clears only the used-bitmap words it dirtied (or its whole bitmap when it
+    # dirtied more than it can list): results of later calls on the same workspace must equal
+    # those of a fresh graph.  Exact full-mode counts of small patterns on 60k vertices dirty
+    # every word of their bitmaps (the overflow path); the early-mode batch lists its words.
+    lab, src, dst = make_graph(kind="cl", nv=60000, ne=300000, nl=4, law="zipf", zipf_s=1.0,
+                               gamma=2.3, seed=53)
+    big = random_patterns(24, range(2, 4), ["tree"], lab, 55)
+    small = random_patterns(60, range(3, 6), SHAPES, lab, 57)
+    full = FULL | fx.FLEXIS_MODE_NO_MNI
+    g = fx.Graph(lab, src, dst)
+    r1 = [key(r) for r in g.support_batch(big, 1, 0.0, full)]
+    # >= 8192 used vertices over 1875 bitmap words: nearly every word is dirtied, more than the
+    # 1024 a pattern's list holds
+    assert max(r[1] for r in r1) > 4096
+    r2 = [key(r) for r in g.support_batch(small, 40, 0.5, EARLY)]
+    r3 = [key(r) for r in g.support_batch(big, 1, 0.0, full)]
+    r4 = [key(r) for r in g.support_batch(small[:7], 40, 0.5, EARLY)]
+    g.close()
+    g2 = fx.Graph(lab, src, dst)
+    assert r2 == [key(r) for r in g2.support_batch(small, 40, 0.5, EARLY)]
+    assert r3 == r1 and r4 == r2[:7]
+    g2.close()
+
+
 def test_no_mni_mode(powerlaw):
     lab, src, dst, pats = powerlaw
     g = fx.Graph(lab, src, dst)
