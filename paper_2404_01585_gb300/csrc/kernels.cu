@@ -631,8 +631,18 @@ __device__ __forceinline__ int block_scan(int v, int &excl, int *sh /* >= 33 int
 
 // Map slots one commit examines: bounds the shared-memory inverted index (the window itself
 // can be larger; slots past the horizon are simply kept for the next round).
+// A round commits at most KM maps of a pattern (the map slots before its horizon).  The inverted
+// index of those maps lives in a shared-memory hash table of 2 * KM * MAXN entries (keys + values:
+// 16 * KM * MAXN bytes).  Small batches, whose windows reach thousands of slots, use KMAP (64 KB
+// per block); large batches, whose windows stay at <= 1024 slots and whose round cost is the
+// per-pattern work of a million active patterns, use KMAP_SMALL (16 KB) in 128-thread blocks, so
+// that about three times as many patterns are committed at once.
 constexpr int KMAP = 512;
-constexpr int COMMIT_HASH = 8192;  // power of two >= 2 * KMAP * MAXN
+constexpr int KMAP_SMALL = 128;
+constexpr int COMMIT_THREADS_SMALL = 128;
+constexpr int SMALL_COMMIT_WMAX = 1024;
+template <int KM>
+constexpr int commit_hash() { return 2 * KM * MAXN; }  // power of two for KM a power of two
 
 __device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
     return ((uint32_t)v * 0x9E3779B1u) >> (32 - logT);
@@ -641,8 +651,9 @@ __device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
 // Commit of one pattern by one block: inverted index of the window's maps, prefix commit, refill,
 // new items.  The window lives in two global buffers per pattern; the kept slots and the refill go
 // to the other buffer, which becomes current for the next search.
+template <int KM>
 __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t *smem) {
-    int32_t *keys = smem, *vals = smem + COMMIT_HASH;
+    int32_t *keys = smem, *vals = smem + commit_hash<KM>();
     __shared__ int sh_scan[40];
     __shared__ int s_f, s_newcur, s_horizon, s_base;
     const int tid = threadIdx.x;
@@ -714,7 +725,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
     }
     __syncthreads();
 
-    // 1. horizon: index of the (KMAP+1)-th map slot (or the window end)
+    // 1. horizon: index of the (KM+1)-th map slot (or the window end)
     if (tid == 0) s_horizon = nwin;
     __syncthreads();
     int nmap = 0;
@@ -723,12 +734,12 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         const int ism = (s < nwin && st_cur[s] == SLOT_MAP) ? 1 : 0;
         int excl;
         const int tot = block_scan(ism, excl, sh_scan);
-        if (ism && nmap + excl == KMAP) s_horizon = s;
+        if (ism && nmap + excl == KM) s_horizon = s;
         nmap += tot;
     }
     __syncthreads();
     const int horizon = s_horizon;
-    const int nins = min(nmap, KMAP) * n;
+    const int nins = min(nmap, KM) * n;
     int logT = 6;
     while ((1 << logT) < 2 * nins) logT++;
     const int T = 1 << logT;
@@ -923,6 +934,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
 // Dense form: one block per pattern slot.  Listed form: blocks walk the list of patterns still in
 // their greedy phase (so late rounds of a large batch launch no block per finished pattern), and
 // append the patterns that stay active to the other list.
+template <int KM>
 __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
     extern __shared__ int32_t smem[];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -931,12 +943,12 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         B.ctl->active[q ^ 1] = 0;
     }
     if (!B.alist) {
-        commit_one(B, q, blockIdx.x, smem);
+        commit_one<KM>(B, q, blockIdx.x, smem);
         return;
     }
     const int count = *reinterpret_cast<volatile int32_t *>(&B.ctl->acount[q]);
     for (int i = blockIdx.x; i < count; i += gridDim.x) {
-        commit_one(B, q, B.alist[(size_t)q * B.P + i], smem);
+        commit_one<KM>(B, q, B.alist[(size_t)q * B.P + i], smem);
         __syncthreads();
     }
 }
@@ -1157,6 +1169,7 @@ struct DeviceGraph {
     cudaGraphExec_t round_exec = nullptr;  // the captured round loop of the last level
     std::vector<cudaEvent_t> gev;          // search-launch events inside the captured graph
     int64_t graph_instantiations = 0, graph_fallbacks = 0;
+    int commit_small_blocks = 0;  // one wave of the small-horizon commit kernel
 };
 
 template <class T>
@@ -1168,7 +1181,9 @@ static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &by
     return FLEXIS_OK;
 }
 
-static size_t commit_smem(int) { return sizeof(int32_t) * 2 * COMMIT_HASH; }
+template <int KM>
+static size_t commit_smem_of() { return sizeof(int32_t) * 2 * commit_hash<KM>(); }
+static size_t commit_smem(int) { return commit_smem_of<KMAP>(); }
 
 int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *bytes) {
     *bytes = (int64_t)g->view.words * 4 + 4ll * DIRTY_CAP + (int64_t)Wmax * (2 * (4 + 4 + 4 * MAXN) + 8) + 8 * KSUSP +
@@ -1209,9 +1224,18 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
         cudaDeviceGetAttribute(&g->l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
         cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)
         return fail(FLEXIS_E_CUDA);
-    if (cudaFuncSetAttribute(k_commit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)commit_smem(0)) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_commit<KMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)commit_smem_of<KMAP>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_commit<KMAP_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)commit_smem_of<KMAP_SMALL>()) != cudaSuccess)
         return fail(FLEXIS_E_CUDA);
+    {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_commit<KMAP_SMALL>, COMMIT_THREADS_SMALL,
+                                                          commit_smem_of<KMAP_SMALL>()) != cudaSuccess)
+            per_sm = 1;
+        g->commit_small_blocks = g->sm_count * std::max(1, per_sm);
+    }
     *out = g;
     return FLEXIS_OK;
 }
@@ -1327,15 +1351,22 @@ static int search_grid(const DeviceGraph *g, const EvalConfig &cfg) {
 // read into g->round_exec, updating the executable graph in place when only the kernel
 // parameters changed.  Returns 0 on success; on any failure the stream is left out of capture,
 // the error is cleared, and the caller launches the kernels one by one.
-static int capture_rounds(DeviceGraph *g, const Batch &B, int R, int commit_blocks, size_t smem, int sblocks,
-                          cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl, const cudaEvent_t *tev) {
+static void launch_commit(const Batch &B, int q, bool small, int commit_blocks, size_t smem, cudaStream_t stream) {
+    if (small)
+        k_commit<KMAP_SMALL><<<commit_blocks, COMMIT_THREADS_SMALL, smem, stream>>>(B, q);
+    else
+        k_commit<KMAP><<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
+}
+
+static int capture_rounds(DeviceGraph *g, const Batch &B, int R, bool small, int commit_blocks, size_t smem,
+                          int sblocks, cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl, const cudaEvent_t *tev) {
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }
     for (int r = 0; r < R; r++) {
-        k_commit<<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, r & 1);
+        launch_commit(B, r & 1, small, commit_blocks, smem, stream);
         // an event record node needs the external flag (a plain record inside a capture only
         // orders streams)
         if (tev) cudaEventRecordWithFlags(tev[2 * r], stream, cudaEventRecordExternal);
@@ -1387,14 +1418,16 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     // large batches walk a list of the patterns still active; small ones launch a block per slot
     const int list_threshold = 4 * g->sm_count;
     if (P > list_threshold) B.alist = w.alist;
-    const int commit_blocks = P > list_threshold ? list_threshold : P;
+    // large batches with windows of <= 1024 slots: the small-horizon commit, one full wave
+    const bool small_commit = P > list_threshold && Wmax <= SMALL_COMMIT_WMAX;
+    const int commit_blocks = small_commit ? g->commit_small_blocks : P > list_threshold ? list_threshold : P;
     if (cfg.search_budget != 0) B.budget = cfg.search_budget < 0 ? 0u : (uint32_t)cfg.search_budget;
     if (cfg.split_pieces != 0) B.split_max = cfg.split_pieces < 0 ? 0 : std::min(cfg.split_pieces, SPLIT_MAX);
     if (cfg.sub_searches > 0) {
         const int k = std::min(cfg.sub_searches, KSUSP);
         B.sid_all = k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1u);
     }
-    const size_t smem = commit_smem(Wmax);
+    const size_t smem = small_commit ? commit_smem_of<KMAP_SMALL>() : commit_smem(Wmax);
     const int sblocks = search_grid(g, cfg);
 
     int64_t launches = 0;
@@ -1439,7 +1472,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
             CK(cudaEventCreate(&e));
             g->gev.push_back(e);
         }
-        if (!capture_rounds(g, B, R, commit_blocks, smem, sblocks, stream, w.h_ctl, w.ctl,
+        if (!capture_rounds(g, B, R, small_commit, commit_blocks, smem, sblocks, stream, w.h_ctl, w.ctl,
                             cfg.timing ? g->gev.data() : nullptr)) {
             for (;;) {
                 CK(cudaGraphLaunch(g->round_exec, stream));
@@ -1466,7 +1499,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     if (!graph_done) for (;;) {
         for (int r = 0; r < R; r++) {
             const int q = (int)(rounds & 1);
-            k_commit<<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
+            launch_commit(B, q, small_commit, commit_blocks, smem, stream);
             if (cfg.timing) {
                 while (evi + 2 > g->sev.size()) {
                     cudaEvent_t e;
@@ -1671,7 +1704,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
     for (int64_t round = 0;;) {
         for (int r = 0; r < 2; r++, round++) {
             const int q = (int)(round & 1);
-            k_commit<<<1, COMMIT_THREADS, commit_smem(0), stream>>>(B, q);
+            k_commit<KMAP><<<1, COMMIT_THREADS, commit_smem(0), stream>>>(B, q);
             k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
         }
         CK(cudaGetLastError());
@@ -1820,7 +1853,7 @@ int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_pl
         k_admit<<<n_admit, 256, 0, s->stream>>>(B, s->d_admit, n_admit);
     }
     const int q = (int)(s->round & 1);
-    k_commit<<<s->slots, COMMIT_THREADS, commit_smem(s->Wmax), s->stream>>>(B, q);
+    k_commit<KMAP><<<s->slots, COMMIT_THREADS, commit_smem(s->Wmax), s->stream>>>(B, q);
     k_search<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
     s->round++;
     k_mni_setup<<<1, 1024, 0, s->stream>>>(B);

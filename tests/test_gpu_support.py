@@ -329,7 +329,9 @@ def test_large_batch_active_list():
                                seed=61)
     pats = random_patterns(1500, range(2, 6), SHAPES, lab, 63)
     og = oracle.Graph(lab, src, dst)
-    for opts in ({}, dict(search_budget=2, window_max=64)):
+    # window_max <= 1024 selects the small-horizon commit (at most 128 maps per pattern and
+    # round); 1024-slot windows from the start make that horizon bind
+    for opts in ({}, dict(search_budget=2, window_max=64), dict(window_min=1024, window_max=1024)):
         g = fx.Graph(lab, src, dst, **opts)
         check_batch(g, og, pats, 20, 0.5, EARLY)
         g.close()
