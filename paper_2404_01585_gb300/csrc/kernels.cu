@@ -642,7 +642,7 @@ constexpr int KMAP_SMALL = 128;
 constexpr int COMMIT_THREADS_SMALL = 128;
 constexpr int SMALL_COMMIT_WMAX = 1024;
 template <int KM>
-constexpr int commit_hash() { return 2 * KM * MAXN; }  // power of two for KM a power of two
+__host__ __device__ constexpr int commit_hash() { return 2 * KM * MAXN; }  // power of two for KM a power of two
 
 __device__ __forceinline__ uint32_t hslot(int32_t v, int logT) {
     return ((uint32_t)v * 0x9E3779B1u) >> (32 - logT);
