@@ -99,7 +99,10 @@ typedef struct {
                                 FLEXIS_E_TIMEOUT.  The limit is checked between rounds of the
                                 greedy phase; the MNI pass of FLEXIS_MODE_FULL is not bounded by
                                 it.  0 = no limit (default). */
-    int32_t reserved[3];
+    int32_t root_order;      /* greedy root order (Sec. 3.2.2): 0 = by (H(seed, v), v), the seeded
+                                hash order (default); 1 = by vertex id, the order in which the
+                                paper's matcher visits the data vertices (seed unused) */
+    int32_t reserved[2];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

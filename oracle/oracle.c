@@ -23,6 +23,9 @@
  *                      (Steele, Lea, Flood 2014).  The mIS is the sequential greedy independent
  *                      set over M in that order (Sec. 2.4.3 maximal independent set; Sec. 3.2.2
  *                      matcher: one match per root, shared used-vertex bitmap).
+ *                      Root-order variant "id" (or_graph_set_root_order): H is dropped, roots
+ *                      are visited in vertex-id order, the order in which the paper's own
+ *                      matcher walks the data graph's vertices (Sec. 3.2.2).
  *   R5 early mode    : counts are reported as min(count, c) with c = max(tau, 1) (Sec. 3.1.1:
  *                      stop once tau is reached); frequent <=> mIS >= max(tau, 1).
  *
@@ -66,6 +69,7 @@ typedef struct {
     int64_t *off;        /* [nv+1] */
     int32_t *nbr;        /* neighbours sorted by id */
     uint64_t seed;
+    int id_order;        /* 1: roots in vertex-id order (no hash key) */
 } or_graph;
 
 static int cmp_i32(const void *a, const void *b)
@@ -126,6 +130,12 @@ void *or_graph_new(int64_t nv, const int32_t *labels, int64_t ne, const int32_t 
     g->off[nv] = k;
     free(deg); free(start); free(tmp); free(fill);
     return g;
+}
+
+/* Root-order variant of R4: id_order = 1 visits roots by vertex id, 0 by (H(seed, v), v). */
+void or_graph_set_root_order(void *gp, int id_order)
+{
+    ((or_graph *)gp)->id_order = id_order ? 1 : 0;
 }
 
 void or_graph_free(void *gp)
@@ -349,13 +359,16 @@ static void maps_brute(const or_graph *g, const or_pat *q, map_list *out)
 /* sort key R4 */
 static const int *g_pi;
 static uint64_t g_seed;
+static int g_id_order;
 static int g_n;
+
+static uint64_t root_key(int32_t r) { return g_id_order ? 0 : or_hash(g_seed, r); }
 
 static int cmp_map_key(const void *pa, const void *pb)
 {
     const or_map *a = pa, *b = pb;
     int32_t ra = a->v[g_pi[0]], rb = b->v[g_pi[0]];
-    uint64_t ha = or_hash(g_seed, ra), hb = or_hash(g_seed, rb);
+    uint64_t ha = root_key(ra), hb = root_key(rb);
     if (ha != hb) return ha < hb ? -1 : 1;
     if (ra != rb) return ra < rb ? -1 : 1;
     for (int k = 1; k < g_n; k++) {
@@ -456,7 +469,7 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
         map_list M = {0};
         maps_brute(g, &q, &M);
         out[3] = M.len;
-        g_pi = pi; g_seed = g->seed; g_n = n;
+        g_pi = pi; g_seed = g->seed; g_id_order = g->id_order; g_n = n;
         qsort(M.a, (size_t)M.len, sizeof *M.a, cmp_map_key);
         /* sequential greedy over the ordered list: keep a map iff none of its vertices is used */
         for (int64_t t = 0; t < M.len; t++) {
@@ -490,7 +503,7 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
         /* insertion into (hash, id) order by a plain sort */
         or_map *tmp = malloc((nr > 0 ? nr : 1) * sizeof *tmp);
         for (int64_t i = 0; i < nr; i++) { memset(&tmp[i], 0, sizeof tmp[i]); tmp[i].v[pi[0]] = roots[i]; }
-        g_pi = pi; g_seed = g->seed; g_n = 1; /* compare by root only */
+        g_pi = pi; g_seed = g->seed; g_id_order = g->id_order; g_n = 1; /* compare by root only */
         qsort(tmp, (size_t)nr, sizeof *tmp, cmp_map_key);
         for (int64_t i = 0; i < nr; i++) roots[i] = tmp[i].v[pi[0]];
         free(tmp);

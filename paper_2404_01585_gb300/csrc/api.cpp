@@ -178,7 +178,7 @@ int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges
     std::unique_ptr<flexis_graph> g(new (std::nothrow) flexis_graph());
     if (!g) return FLEXIS_E_NOMEM;
     if (opt) g->opt = *opt; else flexis_default_options(&g->opt);
-    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->hg);
+    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1, g->hg);
     if (rc) return rc;
     rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
     if (rc) return rc;

@@ -85,7 +85,7 @@ uint64_t root_hash(uint64_t seed, int64_t r);
 
 // host graph construction (graph.cpp)
 int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
-                     const int32_t *dst, uint64_t seed, HostGraph &out);
+                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &out);
 
 // ------------------------------------------------------------------ patterns (pattern.cpp)
 struct Pat {  // small labelled graph, adjacency as bit rows

@@ -41,7 +41,7 @@ static void parallel_for(int64_t n, F f) {
 }
 
 int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
-                     const int32_t *dst, uint64_t seed, HostGraph &g) {
+                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &g) {
     if (nv < 0 || ne < 0 || (nv > 0 && !labels) || (ne > 0 && (!src || !dst)))
         return FLEXIS_E_INVALID;
     if (nv >= (int64_t)INT32_MAX) return FLEXIS_E_UNSUPPORTED;
@@ -160,7 +160,8 @@ int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_
     for (int32_t r = 0; r < g.nl; r++) g.lab_ptr[(size_t)r + 1] += g.lab_ptr[(size_t)r];
     std::vector<uint64_t> hv((size_t)std::max<int64_t>(nv, 1));
     parallel_for(nv, [&](int64_t lo, int64_t hi) {
-        for (int64_t v = lo; v < hi; v++) hv[(size_t)v] = root_hash(seed, v);
+        // root-order variant: by vertex id (the hash key dropped)
+        for (int64_t v = lo; v < hi; v++) hv[(size_t)v] = id_order ? 0 : root_hash(seed, v);
     });
     g.lab_vtx.resize((size_t)std::max<int64_t>(nv, 1));
     {

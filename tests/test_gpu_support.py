@@ -310,6 +310,26 @@ def test_used_bitmaps_left_clean_between_calls():
     g2.close()
 
 
+def test_id_root_order_vs_oracle(powerlaw):
+    # the root-order variant (roots by vertex id): tiny graphs against the brute-force tier, the
+    # power-law batch against the backtracking tier, selected maps one by one
+    for lab, src, dst, pl, pe, s in tiny_cases(40, 23):
+        g = fx.Graph(lab, src, dst, seed=s, root_order=1)
+        og = oracle.Graph(lab, src, dst, seed=s, root_order="id")
+        for mode in (FULL, EARLY):
+            check_batch(g, og, [(pl, pe)], 3, 0.5, mode, tier=0)
+        g.close()
+    lab, src, dst, pats = powerlaw
+    g = fx.Graph(lab, src, dst, root_order=1, record_selected=4096)
+    og = oracle.Graph(lab, src, dst, root_order="id")
+    check_batch(g, og, pats, 60, 0.5, FULL)
+    for i in range(0, 30, 3):
+        pl, pe = pats[i]
+        w = og.support(pl, pe, sigma=60, lam=0.5, mode="full", tier=1, want_selected=True)
+        assert g.selected_maps(i, len(pl), 4096) == w["selected"][:4096]
+    g.close()
+
+
 def test_no_mni_mode(powerlaw):
     lab, src, dst, pats = powerlaw
     g = fx.Graph(lab, src, dst)

@@ -271,6 +271,64 @@ def test_two_vertex_pattern_is_greedy_matching():
             assert r["mis"] == want
 
 
+# ------------------------------------------------------------------ root-order variant: vertex id
+
+def greedy_matching_by_id(lab, src, dst, la, lb):
+    """Textbook greedy maximal matching of the a-b label edges taken in lexicographic order of
+    (a-endpoint, b-endpoint)."""
+    E = sorted({(x, y) for u, v in zip(src.tolist(), dst.tolist()) if u != v
+                for x, y in ((u, v), (v, u)) if lab[x] == la and lab[y] == lb})
+    used, k = set(), 0
+    for x, y in E:
+        if x not in used and y not in used:
+            used |= {x, y}
+            k += 1
+    return k
+
+
+def test_id_root_order_tiers_agree_and_invariants():
+    differs = 0
+    for lab, src, dst, pl, pe, s in tiny_cases(120, 23):
+        edges = list(zip(src.tolist(), dst.tolist()))
+        M = bf.maps(lab.tolist(), edges, pl, pe)
+        g = oracle.Graph(lab, src, dst, seed=s, root_order="id")
+        gh = oracle.Graph(lab, src, dst, seed=s)
+        r0 = g.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=0, want_selected=True)
+        r1 = g.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=1, want_selected=True)
+        assert (r0["mis"], r0["mni"], r0["selected"]) == (r1["mis"], r1["mni"], r1["selected"])
+        assert bf.is_independent(r1["selected"]) and bf.is_maximal(r1["selected"], M)
+        assert r1["mis"] <= r1["mni"] == bf.mni(M, len(pl))
+        # the seed plays no part in id order
+        g2 = oracle.Graph(lab, src, dst, seed=s + 12345, root_order="id")
+        assert g2.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=1, want_selected=True)["selected"] == r1["selected"]
+        differs += gh.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=1, want_selected=True)["selected"] != r1["selected"]
+    assert differs > 0  # the two orders are really different orders
+
+
+def test_id_root_order_two_vertex_pattern_is_lexicographic_greedy_matching():
+    for lab, src, dst, _, _, s in tiny_cases(60, 37):
+        if len(set(lab.tolist())) < 2:
+            continue
+        g = oracle.Graph(lab, src, dst, seed=s, root_order="id")
+        a, b = sorted(set(lab.tolist()))[:2]
+        ca, cb = int((lab == a).sum()), int((lab == b).sum())
+        ra, rb = (a, b) if (ca, a) < (cb, b) else (b, a)
+        want = greedy_matching_by_id(lab, src, dst, ra, rb)
+        for tier in (0, 1):
+            assert g.support([a, b], [(0, 1)], sigma=1, lam=1.0, mode="full", tier=tier)["mis"] == want
+
+
+def test_id_root_order_path_closed_form():
+    # a one-label path 0-1-...-(k-1): in id order root 0 takes edge (0,1), root 2 takes (2,3), ...
+    for k in (2, 3, 7, 10, 31):
+        lab = np.zeros(k, np.int32)
+        src = np.arange(k - 1, dtype=np.int32)
+        g = oracle.Graph(lab, src, src + 1, root_order="id")
+        r = g.support([0, 0], [(0, 1)], sigma=1, lam=1.0, mode="full", tier=1, want_selected=True)
+        assert r["mis"] == k // 2
+        assert sorted(tuple(sorted(m)) for m in r["selected"]) == [(2 * i, 2 * i + 1) for i in range(k // 2)]
+
+
 # ----------------------------------------------------------------------------- canonical code
 
 def nxg(labels, edges):
