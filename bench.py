@@ -208,6 +208,21 @@ def serving_leg(g, fx, lab, nq=2000, rates=(0.3, 0.6, 0.9), seed=2005, per_rate_
     return out
 
 
+def reduce_over_ranks(dist, ms, count):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks.  Returns
+    (max ms, summed count, count per second).  `dist` is torch.distributed or None (one rank)."""
+    import torch
+    t_max, c_all = float(ms), int(count)
+    if dist:
+        tt = torch.tensor([t_max], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        cc = torch.tensor([c_all], dtype=torch.float64)
+        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+        c_all = int(cc.item())
+    return t_max, c_all, c_all / (t_max / 1e3)
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -314,16 +329,7 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    t_max = ms
-    c_all = total_c
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        cc = torch.tensor([total_c], dtype=torch.float64)
-        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
-        c_all = int(cc.item())
-    value = c_all / (t_max / 1e3)
+    t_max, c_all, value = reduce_over_ranks(dist, ms, total_c)
 
     # roofline of the greedy search kernel
     peak, peak_kind = peaks()
