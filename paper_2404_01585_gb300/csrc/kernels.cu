@@ -3,9 +3,10 @@
 // What is computed (per pattern, all integer):
 //   mIS  : the greedy maximal independent set of the pattern's maps (Sec. 2.4.3) taken in the
 //          fixed order (H(seed, root), root, lexicographic tuple in matching order): roots are
-//          visited in hash order, each root selects its lexicographically first map that avoids
-//          vertices already used and then stops (Sec. 3.2.2, changes 1 and 2).  EARLY mode
-//          stops at c = max(tau, 1) selections (Sec. 3.1.1).
+//          visited in hash order (or by vertex id, the root-order variant; the order lives only
+//          in the host-built root index), each root selects its lexicographically first map that
+//          avoids vertices already used and then stops (Sec. 3.2.2, changes 1 and 2).  EARLY
+//          mode stops at c = max(tau, 1) selections (Sec. 3.1.1).
 //   MNI  : min over automorphism orbits of the number of distinct data vertices that some map
 //          sends the orbit's vertices to (Sec. 2.4.4).
 //   tau / frequent (Eq. tau).
