@@ -102,7 +102,11 @@ typedef struct {
     int32_t root_order;      /* greedy root order (Sec. 3.2.2): 0 = by (H(seed, v), v), the seeded
                                 hash order (default); 1 = by vertex id, the order in which the
                                 paper's matcher visits the data vertices (seed unused) */
-    int32_t reserved[2];
+    int32_t search_variant;  /* membership tests of the batched search: 0 = binary search (default);
+                                1 = interpolation search guarded by bisection, with the candidate's
+                                used-bit and vertex-record loads issued together.  Results are
+                                identical; 1 is checked on the host and not yet timed on a GPU */
+    int32_t reserved[1];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

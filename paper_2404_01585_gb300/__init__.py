@@ -48,7 +48,7 @@ class flexis_options(C.Structure):
                 ("record_selected", C.c_int32), ("search_budget", C.c_int32),
                 ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("timing", C.c_int32),
                 ("graphs", C.c_int32), ("deadline_ms", C.c_int32), ("root_order", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("search_variant", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class flexis_pattern(C.Structure):

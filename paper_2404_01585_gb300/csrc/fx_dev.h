@@ -20,6 +20,7 @@ struct EvalConfig {
     bool timing = false;        // per-launch CUDA events around the search kernel
     bool graphs = true;         // replay the round loop as a captured CUDA graph
     int32_t deadline_ms = 0;    // > 0: patterns undecided after this long stop with FLEXIS_E_TIMEOUT
+    int32_t search_variant = 0; // 1: interpolation-search membership tests (see search_util.h)
 };
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);

@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "fx_dev.h"
+#include "search_util.h"
 
 namespace fx {
 
@@ -242,6 +243,7 @@ __device__ __forceinline__ bool vertex_fits(const DevGraphView &G, int32_t c, ui
 
 // Candidate test at level i.  rej collects the earlier levels whose bound vertex caused a
 // rejection by injectivity (the conflict set of conflict-directed backjumping).
+template <int V>
 __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
                                                 int32_t c, const uint32_t *used,
                                                 uint32_t &probes, uint32_t &rej) {
@@ -250,6 +252,24 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
         const int b = __ffs(im) - 1;
         im &= im - 1;
         if (W.t[b] == c) { rej |= 1u << b; return false; }
+    }
+    if constexpr (V == 1) {
+        // the used word and the vertex record do not depend on each other: load both before
+        // either decides, then test membership by interpolation search (same answers)
+        const uint32_t uw = used ? __ldcg(used + ((uint32_t)c >> 5)) : 0u;
+        const VRec *r = G.vrec + c;
+        const uint32_t deg = __ldg(&r->deg);
+        const unsigned long long have = __ldg(reinterpret_cast<const unsigned long long *>(&r->nbr_labels));
+        probes += used ? 5u : 4u;
+        if ((uw >> ((uint32_t)c & 31u)) & 1u) return false;
+        const unsigned long long need = W.need[W.L.vert[i]];
+        if (deg < W.L.deg[i] || (have & need) != need) return false;
+        const int nchk = W.nchk[i];
+        const int32_t *adj = G.adj;
+        auto at = [adj](uint32_t x) { return __ldg(adj + x); };
+        for (int k = 0; k < nchk; k++)
+            if (!interp_contains(at, W.clo[i][k], W.chi[i][k], c, probes)) return false;
+        return true;
     }
     if (used) {
         probes++;
@@ -283,6 +303,8 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // found is the first map avoiding the current used set.
 enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
 
+// V selects the membership test of check_candidate (0: binary search, 1: interpolation search).
+template <int V>
 __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                        unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
                        bool resume) {
@@ -340,7 +362,7 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
             const uint32_t k = pos + lane;
             bool good = false;
             uint32_t rej = 0;
-            if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes, rej);
+            if (k < hi) good = check_candidate<V>(G, W, i, __ldg(G.adj + k), used, probes, rej);
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
             bytes += 4ull * min(32u, hi - pos);
@@ -371,7 +393,7 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
 __device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
                                           int32_t root, unsigned long long &bytes, uint32_t &probes,
                                           uint32_t &steps) {
-    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
+    return dfs_run<0>(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
 }
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {
@@ -468,6 +490,7 @@ __device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, in
 // A search that uses up its per-round budget is saved; if it heads its slot it is also split:
 // the unscanned candidates of its shallowest level with any left go to up to five new
 // sub-searches, in order, and a continuation takes over everything after them.
+template <int V>
 __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     __shared__ WarpState ws[SEARCH_THREADS / 32];
     const int lane = threadIdx.x & 31;
@@ -499,7 +522,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
+        int r = dfs_run<V>(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
         int sidA = sid_in;
         if (r == DFS_SUSPENDED) {
             const bool head = !resume || seq[0] == sid_in;
@@ -1343,7 +1366,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
 
 static int search_grid(const DeviceGraph *g, const EvalConfig &cfg) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, SEARCH_THREADS, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<0>, SEARCH_THREADS, 0) != cudaSuccess)
         per_sm = 1;
     return cfg.search_blocks > 0 ? cfg.search_blocks : g->sm_count * std::max(1, per_sm);
 }
@@ -1359,8 +1382,16 @@ static void launch_commit(const Batch &B, int q, bool small, int commit_blocks, 
         k_commit<KMAP><<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
 }
 
+static void launch_search(const Batch &B, int q, int variant, int sblocks, cudaStream_t stream) {
+    if (variant == 1)
+        k_search<1><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+    else
+        k_search<0><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+}
+
 static int capture_rounds(DeviceGraph *g, const Batch &B, int R, bool small, int commit_blocks, size_t smem,
-                          int sblocks, cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl, const cudaEvent_t *tev) {
+                          int variant, int sblocks, cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl,
+                          const cudaEvent_t *tev) {
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1371,7 +1402,7 @@ static int capture_rounds(DeviceGraph *g, const Batch &B, int R, bool small, int
         // an event record node needs the external flag (a plain record inside a capture only
         // orders streams)
         if (tev) cudaEventRecordWithFlags(tev[2 * r], stream, cudaEventRecordExternal);
-        k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, r & 1);
+        launch_search(B, r & 1, variant, sblocks, stream);
         if (tev) cudaEventRecordWithFlags(tev[2 * r + 1], stream, cudaEventRecordExternal);
     }
     cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
@@ -1473,7 +1504,8 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
             CK(cudaEventCreate(&e));
             g->gev.push_back(e);
         }
-        if (!capture_rounds(g, B, R, small_commit, commit_blocks, smem, sblocks, stream, w.h_ctl, w.ctl,
+        if (!capture_rounds(g, B, R, small_commit, commit_blocks, smem, cfg.search_variant, sblocks, stream,
+                            w.h_ctl, w.ctl,
                             cfg.timing ? g->gev.data() : nullptr)) {
             for (;;) {
                 CK(cudaGraphLaunch(g->round_exec, stream));
@@ -1509,7 +1541,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
                 }
                 CK(cudaEventRecord(g->sev[evi], stream));
             }
-            k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+            launch_search(B, q, cfg.search_variant, sblocks, stream);
             if (cfg.timing) {
                 CK(cudaEventRecord(g->sev[evi + 1], stream));
                 evi += 2;
@@ -1706,7 +1738,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
         for (int r = 0; r < 2; r++, round++) {
             const int q = (int)(round & 1);
             k_commit<KMAP><<<1, COMMIT_THREADS, commit_smem(0), stream>>>(B, q);
-            k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+            k_search<0><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&h_ctl, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
@@ -1855,7 +1887,7 @@ int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_pl
     }
     const int q = (int)(s->round & 1);
     k_commit<KMAP><<<s->slots, COMMIT_THREADS, commit_smem(s->Wmax), s->stream>>>(B, q);
-    k_search<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
+    k_search<0><<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
     s->round++;
     k_mni_setup<<<1, 1024, 0, s->stream>>>(B);
     k_mni<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B);
