@@ -5,6 +5,7 @@
 #include <array>
 #include <atomic>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -346,42 +347,96 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
     out.clear();
     if (F.empty()) return;
     std::unordered_set<Code, CodeHash> Fset(F.begin(), F.end());
-    // core groups
-    std::unordered_map<Code, size_t, CodeHash> gidx;
-    std::vector<Group> groups;
-    std::vector<int32_t> labels;
-    for (const Code &c : F) {
-        Pat P = pat_of_code(c);
-        for (int i = 0; i < P.n; i++) labels.push_back(P.lab[i]);
-        for (int x = 0; x < P.n; x++) {
-            Pat core;
-            core.n = P.n - 1;
-            int pos[MAXN], k = 0;
-            for (int i = 0; i < P.n; i++)
-                if (i != x) pos[k++] = i;
-            for (int i = 0; i < core.n; i++) {
-                core.lab[i] = P.lab[pos[i]];
-                for (int j = 0; j < core.n; j++)
-                    if (has(P, pos[i], pos[j])) core.adj[i] |= (uint8_t)(1 << j);
-            }
-            int perm[MAXN];
-            Code cc = canonical(core, perm);
-            // attachment of x over the core's canonical positions
-            uint8_t mask = 0;
-            for (int cp = 0; cp < core.n; cp++)
-                if (has(P, x, pos[perm[cp]])) mask |= (uint8_t)(1 << cp);
-            auto it = gidx.find(cc);
-            size_t gi;
-            if (it == gidx.end()) {
-                gi = groups.size();
-                gidx.emplace(cc, gi);
-                groups.push_back(Group{cc, {}, {}});
-            } else {
-                gi = it->second;
-            }
-            groups[gi].entries.push_back(CoreEntry{P.lab[x], mask});
+    const int T = std::max(1, threads);
+    auto parallel = [&](size_t count, const std::function<void(int, size_t, size_t)> &body) {
+        std::vector<std::thread> th;
+        const size_t per = (count + (size_t)T - 1) / (size_t)T;
+        for (int t = 1; t < T; t++) {
+            const size_t lo = std::min(count, per * (size_t)t), hi = std::min(count, lo + per);
+            th.emplace_back(body, t, lo, hi);
         }
+        body(0, 0, std::min(count, per));
+        for (auto &x : th) x.join();
+    };
+    // core groups: every (member, removed vertex) gives a core in canonical form and the removed
+    // vertex's label and attachment over the core's canonical positions; computed per thread,
+    // then grouped by sorting on the core
+    struct CoreRec {
+        Code core;
+        CoreEntry e;
+    };
+    std::vector<size_t> first((size_t)F.size() + 1, 0);
+    for (size_t f = 0; f < F.size(); f++) first[f + 1] = first[f] + (size_t)F[f].n;
+    std::vector<CoreRec> recs(first.back());
+    parallel(F.size(), [&](int, size_t lo, size_t hi) {
+        for (size_t f = lo; f < hi; f++) {
+            const Pat P = pat_of_code(F[f]);
+            for (int x = 0; x < P.n; x++) {
+                Pat core;
+                core.n = P.n - 1;
+                int pos[MAXN], k = 0;
+                for (int i = 0; i < P.n; i++)
+                    if (i != x) pos[k++] = i;
+                for (int i = 0; i < core.n; i++) {
+                    core.lab[i] = P.lab[pos[i]];
+                    for (int j = 0; j < core.n; j++)
+                        if (has(P, pos[i], pos[j])) core.adj[i] |= (uint8_t)(1 << j);
+                }
+                int perm[MAXN];
+                const Code cc = canonical(core, perm);
+                uint8_t mask = 0;
+                for (int cp = 0; cp < core.n; cp++)
+                    if (has(P, x, pos[perm[cp]])) mask |= (uint8_t)(1 << cp);
+                recs[first[f] + (size_t)x] = CoreRec{cc, CoreEntry{P.lab[x], mask}};
+            }
+        }
+    });
+    // group: records are spread over buckets by the core's hash (equal cores share a bucket),
+    // each bucket is sorted and cut into groups in parallel; the order of the groups does not
+    // matter (every group's candidates end in the sorted, deduplicated output)
+    const size_t nb = (size_t)T * 8;
+    std::vector<size_t> bstart(nb + 1, 0);
+    std::vector<uint32_t> bucket_of(recs.size());
+    CodeHash hasher;
+    for (size_t i = 0; i < recs.size(); i++) {
+        bucket_of[i] = (uint32_t)(hasher(recs[i].core) % nb);
+        bstart[bucket_of[i] + 1]++;
     }
+    for (size_t b = 0; b < nb; b++) bstart[b + 1] += bstart[b];
+    std::vector<CoreRec> byb(recs.size());
+    {
+        std::vector<size_t> fill(bstart.begin(), bstart.end() - 1);
+        for (size_t i = 0; i < recs.size(); i++) byb[fill[bucket_of[i]]++] = recs[i];
+    }
+    std::vector<CoreRec>().swap(recs);
+    std::vector<std::vector<Group>> bgroups(nb);
+    {
+        std::atomic<size_t> next_b{0};
+        auto worker = [&] {
+            for (size_t b; (b = next_b.fetch_add(1)) < nb;) {
+                auto lo = byb.begin() + (ptrdiff_t)bstart[b], hi = byb.begin() + (ptrdiff_t)bstart[b + 1];
+                std::sort(lo, hi, [](const CoreRec &x, const CoreRec &y) {
+                    if (!(x.core == y.core)) return x.core < y.core;
+                    return x.e < y.e;
+                });
+                for (auto it = lo; it != hi; ++it) {
+                    if (it == lo || !(it->core == (it - 1)->core)) bgroups[b].push_back(Group{it->core, {}, {}});
+                    bgroups[b].back().entries.push_back(it->e);
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; t++) th.emplace_back(worker);
+        worker();
+        for (auto &x : th) x.join();
+    }
+    std::vector<CoreRec>().swap(byb);
+    std::vector<Group> groups;
+    for (auto &v : bgroups)
+        for (auto &gr : v) groups.push_back(std::move(gr));
+    std::vector<int32_t> labels;
+    for (const Code &c : F)
+        for (int i = 0; i < c.n; i++) labels.push_back(c.lab[i]);
     std::sort(labels.begin(), labels.end());
     labels.erase(std::unique(labels.begin(), labels.end()), labels.end());
 
@@ -437,11 +492,12 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
         std::sort(local.begin(), local.end());
         local.erase(std::unique(local.begin(), local.end()), local.end());
     };
-    int T = std::max(1, threads);
-    std::vector<std::thread> th;
-    for (int t = 1; t < T; t++) th.emplace_back(work, t);
-    work(0);
-    for (auto &t : th) t.join();
+    {
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; t++) th.emplace_back(work, t);
+        work(0);
+        for (auto &t : th) t.join();
+    }
     std::vector<Code> cliques;
     // cliques (Algorithm 4 + post-check): a k-clique whose every (k-1)-sub-clique is frequent
     for (const Code &c : F) {
@@ -475,25 +531,60 @@ void generate_candidates(const std::vector<Code> &F, int max_edges, std::vector<
     }
     std::sort(cliques.begin(), cliques.end());
     part.push_back(std::move(cliques));
-    // union of the sorted runs (one per thread, plus the cliques): a k-way merge that drops
-    // repeats, so the output comes out sorted and unique
-    size_t total = 0;
-    for (auto &v : part) total += v.size();
-    out.reserve(total);
-    std::vector<size_t> at(part.size(), 0);
-    auto run_less = [&](size_t a, size_t b) { return part[b][at[b]] < part[a][at[a]]; };  // min-heap
-    std::vector<size_t> heap;
+    // union of the sorted runs (one per thread, plus the cliques): the key space is cut at
+    // splitters taken from the largest run; each piece is a k-way merge that drops repeats, run
+    // in parallel, and the pieces are concatenated in key order (sorted and unique overall)
+    size_t big = 0;
     for (size_t r = 0; r < part.size(); r++)
-        if (!part[r].empty()) heap.push_back(r);
-    std::make_heap(heap.begin(), heap.end(), run_less);
-    while (!heap.empty()) {
-        std::pop_heap(heap.begin(), heap.end(), run_less);
-        const size_t r = heap.back();
-        const Code &c = part[r][at[r]];
-        if (out.empty() || !(out.back() == c)) out.push_back(c);
-        if (++at[r] < part[r].size()) std::push_heap(heap.begin(), heap.end(), run_less);
-        else heap.pop_back();
+        if (part[r].size() > part[big].size()) big = r;
+    std::vector<Code> split;  // piece p holds keys in [split[p-1], split[p])
+    const size_t pieces = part[big].size() > 4096 ? (size_t)T * 4 : 1;
+    for (size_t p = 1; p < pieces; p++) split.push_back(part[big][part[big].size() * p / pieces]);
+    split.erase(std::unique(split.begin(), split.end()), split.end());
+    const size_t np = split.size() + 1;
+    std::vector<std::vector<Code>> merged(np);
+    auto merge_piece = [&](size_t p) {
+        std::vector<std::pair<size_t, size_t>> rng(part.size());  // [begin, end) of each run
+        for (size_t r = 0; r < part.size(); r++) {
+            const auto &v = part[r];
+            const size_t b = p == 0 ? 0 : (size_t)(std::lower_bound(v.begin(), v.end(), split[p - 1]) - v.begin());
+            const size_t e = p + 1 == np ? v.size() : (size_t)(std::lower_bound(v.begin(), v.end(), split[p]) - v.begin());
+            rng[r] = {b, e};
+        }
+        auto run_less = [&](size_t a, size_t b) { return part[b][rng[b].first] < part[a][rng[a].first]; };
+        std::vector<size_t> heap;
+        size_t total = 0;
+        for (size_t r = 0; r < part.size(); r++)
+            if (rng[r].first < rng[r].second) {
+                heap.push_back(r);
+                total += rng[r].second - rng[r].first;
+            }
+        std::vector<Code> &o = merged[p];
+        o.reserve(total);
+        std::make_heap(heap.begin(), heap.end(), run_less);
+        while (!heap.empty()) {
+            std::pop_heap(heap.begin(), heap.end(), run_less);
+            const size_t r = heap.back();
+            const Code &c = part[r][rng[r].first];
+            if (o.empty() || !(o.back() == c)) o.push_back(c);
+            if (++rng[r].first < rng[r].second) std::push_heap(heap.begin(), heap.end(), run_less);
+            else heap.pop_back();
+        }
+    };
+    {
+        std::atomic<size_t> next_piece{0};
+        auto worker = [&] {
+            for (size_t p; (p = next_piece.fetch_add(1)) < np;) merge_piece(p);
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; t++) th.emplace_back(worker);
+        worker();
+        for (auto &x : th) x.join();
     }
+    size_t total = 0;
+    for (auto &v : merged) total += v.size();
+    out.reserve(total);
+    for (auto &v : merged) out.insert(out.end(), v.begin(), v.end());
 }
 
 }  // namespace fx
