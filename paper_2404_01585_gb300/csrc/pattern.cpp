@@ -62,7 +62,11 @@ int edge_count(const Pat &p) {
 // i = 0..j-1 the bit "not adjacent"; the canonical code is the lexicographic minimum over all
 // orders.  Search: positions are filled left to right; the label of each position is forced
 // (sorted label multiset), and a partial order whose bit prefix already exceeds the best
-// prefix is pruned.  The minimum over the pruned search equals the minimum over all n! orders.
+// prefix is pruned.  Twins -- two vertices of one label with the same neighbours apart from
+// each other -- are exchanged by an automorphism that fixes every other vertex, so at each
+// position only the lowest-numbered unused vertex of a set of twins is tried: the orders skipped
+// are images of tried ones under that automorphism and give the same codes.  The minimum over
+// the pruned search equals the minimum over all n! orders.
 namespace {
 struct CanonSearch {
     const Pat *p;
@@ -73,6 +77,7 @@ struct CanonSearch {
     uint32_t best_bits;
     bool have;
     int total_bits;
+    uint32_t twin_below[MAXN];  // lower-numbered twins of each vertex
 
     void rec(int pos, int used, uint32_t bits, int nb) {
         if (pos == n) {
@@ -87,6 +92,7 @@ struct CanonSearch {
         for (int w = 0; w < n; w++) {
             if (used >> w & 1) continue;
             if (p->lab[w] != slab[pos]) continue;
+            if (twin_below[w] & ~(uint32_t)used) continue;  // an unused lower twin stands for w
             uint32_t b = bits;
             for (int i = 0; i < pos; i++) b = (b << 1) | (has(*p, perm[i], w) ? 0u : 1u);
             int nb2 = nb + pos;
@@ -108,6 +114,13 @@ Code canonical(const Pat &p, int *perm) {
     s.have = false;
     s.best_bits = 0;
     s.total_bits = p.n * (p.n - 1) / 2;
+    for (int w = 0; w < p.n; w++) {
+        s.twin_below[w] = 0;
+        for (int u = 0; u < w; u++)
+            if (p.lab[u] == p.lab[w] &&
+                (p.adj[u] & ~(uint8_t)(1u << w)) == (p.adj[w] & ~(uint8_t)(1u << u)))
+                s.twin_below[w] |= 1u << u;
+    }
     s.rec(0, 0, 0, 0);
     Code c;
     c.n = p.n;

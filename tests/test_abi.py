@@ -69,6 +69,42 @@ def test_canonical_code_matches_oracle():
         assert a[:2] == b[:2]
 
 
+def test_canonical_code_of_symmetric_patterns_matches_oracle():
+    # stars, cliques, cycles, complete bipartite graphs and their one-label / two-label versions
+    # have many twins and automorphisms (the search skips twins)
+    st = Stream(77)
+    shapes = []
+    for n in range(2, 9):
+        shapes.append((n, [(0, i) for i in range(1, n)]))
+        shapes.append((n, [(i, j) for i in range(n) for j in range(i + 1, n)]))
+        if n >= 3:
+            shapes.append((n, [(i, (i + 1) % n) for i in range(n)]))
+        for k in range(1, n):
+            shapes.append((n, [(i, j) for i in range(k) for j in range(k, n)]))
+    for n, e in shapes:
+        for labels in (1, 2, 3):
+            for _ in range(4):
+                lab = [int(x) for x in st.integers(n, labels)]
+                perm = [int(x) for x in st.permutation(n)]
+                pe = [(perm[a], perm[b]) for a, b in e]
+                pl = [0] * n
+                for u in range(n):
+                    pl[perm[u]] = lab[u]
+                a = fx.canonical_code(pl, pe)
+                b = oracle.canonical(pl, pe)
+                assert a[:2] == b[:2], (pl, pe)
+                # the returned order realises the code
+                order = list(a[2])
+                assert sorted(order) == list(range(n))
+                assert [pl[v] for v in order] == list(a[0])
+                adj = {(x, y) for x, y in pe} | {(y, x) for x, y in pe}
+                bits, t = 0, 0
+                for j in range(1, n):
+                    for i in range(j):
+                        bits = (bits << 1) | (0 if (order[i], order[j]) in adj else 1)
+                assert bits == a[1]
+
+
 def test_candidate_generation_paper_figures():
     R, B, G, Y = 0, 1, 2, 3
     tri = [(0, 1), (1, 2), (0, 2)]
