@@ -6,7 +6,10 @@ with the host sources it tests and compared there with a plain recomputation.
   bisection bound on the loads it makes.
 * host_graph_check.cpp -- the data-graph build (csrc/graph.cpp): label ranks, deduplicated and
   sorted adjacency, label runs, vertex records, the root index in both root orders, label pairs,
-  dropped self-loops and repeats, on 144 random graphs."""
+  dropped self-loops and repeats, on 144 random graphs.
+* host_plan_check.cpp -- the pattern compiler (csrc/pattern.cpp): matching orders and their
+  masks from their definitions, orbit representatives against brute-force automorphisms, label
+  slices, neighbour-label sets, tau special cases, absent labels and invalid inputs."""
 from __future__ import annotations
 
 import os
@@ -40,3 +43,7 @@ def test_interpolation_search_matches_binary_search():
 
 def test_host_graph_build_matches_plain_recomputation():
     run_check("host_graph_check.cpp", "graph.cpp")
+
+
+def test_host_pattern_compiler_matches_definitions():
+    run_check("host_plan_check.cpp", "pattern.cpp", "graph.cpp")
