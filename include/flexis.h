@@ -31,7 +31,8 @@
  *     order (H(seed, root), root, lexicographic tuple in matching order), root = image of
  *     canonical vertex 0, H = one SplitMix64 step from state seed XOR root.  Per root the first
  *     map avoiding used vertices is selected and the root's search stops (Sec. 3.2.2, change 1);
- *     used vertices are shared across roots (Sec. 3.2.2, change 2).
+ *     used vertices are shared across roots (Sec. 3.2.2, change 2).  options.root_order = 1
+ *     drops H: roots are then visited by vertex id.
  *   - tau = floor(sigma * ((n-1) * p + q) / (n * q)) exactly, lambda = p / q, q = 10^6 and
  *     p = llround(lambda * 10^6) for the double-valued entry points.
  *   - Frequent <=> mIS >= max(tau, 1).
@@ -51,7 +52,8 @@ extern "C" {
                                      n>8, lambda outside [0,1] or NaN, sigma < 1, null pointer */
 #define FLEXIS_E_NOMEM (-2)       /* a host or device allocation failed */
 #define FLEXIS_E_CUDA (-3)        /* a CUDA runtime call failed (no device, launch error) */
-#define FLEXIS_E_TIMEOUT (-4)     /* a bounded device or host wait gave up */
+#define FLEXIS_E_TIMEOUT (-4)     /* a bounded wait gave up, or a pattern / request / mining run
+                                     passed options.deadline_ms before its decision */
 #define FLEXIS_E_CANCELLED (-5)   /* a served request was cancelled / server stopped */
 #define FLEXIS_E_UNSUPPORTED (-6) /* graph beyond the layout limits (see flexis_load_graph) */
 #define FLEXIS_E_BUSY (-7)        /* serving queue full; retry later */
@@ -168,8 +170,9 @@ typedef struct {
     int64_t patterns;         /* patterns evaluated by the call */
     int64_t h2d_bytes;        /* bytes copied host -> device (plans) */
     int64_t d2h_bytes;        /* bytes copied device -> host (results, control words) */
-    float search_ms;          /* summed CUDA-event time of the greedy search kernel launches */
-    float mni_ms;             /* CUDA-event time of the MNI kernel */
+    float search_ms;          /* summed CUDA-event time of the greedy search kernel launches
+                                 (measured with options.timing = 1, else 0) */
+    float mni_ms;             /* CUDA-event time of the MNI kernel (options.timing = 1) */
     float total_ms;           /* CUDA-event time of the device sections */
     float host_gen_ms;        /* host time in candidate generation (mining) */
     float host_compile_ms;    /* host time in pattern compilation */
