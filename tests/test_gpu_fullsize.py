@@ -1,8 +1,9 @@
 """GPU parity at the benchmark's full sizes, in the launch configuration bench.py times.
 
-* MiCo-shaped graph (100,000 vertices, 1,080,000 edges, 29 labels): the whole frequent-pattern
-  set of the mining loop up to 3 edges equals the oracle's (exact, every pattern and value);
-  up to 5 edges, a deterministic sample of the frequent patterns is re-evaluated by the oracle.
+* MiCo-shaped graph (100,000 vertices, 1,080,000 edges, 29 labels), sigma = 3000 at lambda = 0.5
+  and lambda = 0: the whole frequent-pattern set of the mining loop up to 3 edges equals the
+  oracle's (exact, every pattern and value); up to 5 edges, a deterministic sample of the
+  frequent patterns is re-evaluated by the oracle.
 * The 1 M-vertex batched level (2,000 trees / cycles / cliques of 3-7 vertices): the oracle
   re-evaluates the patterns it finishes in seconds (<= 4 vertices); for every pattern the
   selected maps themselves are checked against properties that hold at any size -- each is a
@@ -33,28 +34,30 @@ def mico():
     return make_graph("mico")
 
 
-def test_mico_mining_exact_to_3_edges(mico):
+@pytest.mark.parametrize("lam", [0.5, 0.0])
+def test_mico_mining_exact_to_3_edges(mico, lam):
     lab, src, dst = mico
     g = fx.Graph(lab, src, dst)
     og = oracle.Graph(lab, src, dst)
-    got, glev = g.mine(3000, 0.5, 3)
-    want, wlev = og.mine(sigma=3000, lam=0.5, max_edges=3)
+    got, glev = g.mine(3000, lam, 3)
+    want, wlev = og.mine(sigma=3000, lam=lam, max_edges=3)
     assert glev == wlev
     assert [(p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in got] == want
     g.close()
 
 
-def test_mico_mining_sampled_to_5_edges(mico):
+@pytest.mark.parametrize("lam", [0.5, 0.0])
+def test_mico_mining_sampled_to_5_edges(mico, lam):
     lab, src, dst = mico
     g = fx.Graph(lab, src, dst)
     og = oracle.Graph(lab, src, dst)
-    got, levels = g.mine(3000, 0.5, 5)
+    got, levels = g.mine(3000, lam, 5)
     assert levels[6][1] > 0  # the sweep really reaches 6-vertex patterns
     for p in got:
         assert p["mis"] == p["tau"] and p["mni"] == p["tau"]  # frequent: counts capped at tau
     sample = [p for p in got if p["n"] >= 5][::max(1, len([p for p in got if p["n"] >= 5]) // 12)][:12]
     for p in sample:
-        w = og.support(list(p["labels"]), p["edges"], sigma=3000, lam=0.5, mode="early", tier=1)
+        w = og.support(list(p["labels"]), p["edges"], sigma=3000, lam=lam, mode="early", tier=1)
         assert (w["tau"], w["mis"], w["mni"], w["frequent"]) == (p["tau"], p["mis"], p["mni"], True), p
     g.close()
 
