@@ -190,7 +190,12 @@ def default_options(**kw) -> flexis_options:
 
 
 class Graph:
-    """A data graph resident on one GPU (flexis_load_graph)."""
+    """A data graph resident on one GPU (flexis_load_graph).
+
+    Keyword options are the fields of flexis_options: seed, device, window_min, window_max,
+    search_blocks, record_selected, search_budget, split_pieces, sub_searches, timing, graphs,
+    deadline_ms, root_order, search_variant (meanings in include/flexis.h).  They apply to every
+    call on the graph and to servers started on it."""
 
     def __init__(self, labels, src, dst, **options):
         L = lib()
