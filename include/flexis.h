@@ -184,6 +184,13 @@ typedef struct {
 
 const char *flexis_status_string(int status);
 
+/* lambda as the exact rational num / FLEXIS_LAMBDA_DEN used by every double-valued entry point
+ * (Eq. tau takes lambda in [0, 1]): num = llround(lambda * 10^6), i.e. halves round away from
+ * zero.  FLEXIS_E_INVALID for lambda outside [0, 1] or NaN (num_out untouched).  Callers that
+ * compile plans with flexis_compile use this to get the same tau as flexis_support.           */
+#define FLEXIS_LAMBDA_DEN 1000000
+int flexis_lambda_quantize(double lambda, int64_t *num_out);
+
 /* Fill *opt with the defaults. */
 void flexis_default_options(flexis_options *opt);
 
@@ -240,6 +247,8 @@ int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int
  *   plan   : host pointer to one plan from flexis_compile (the caller passes the input)
  *   out    : host pointer, receives the result (same values as flexis_support on that pattern)
  *   stream : cudaStream_t to run on, NULL = the graph's stream; the call synchronises it
+ * The graph's options.deadline_ms applies as in flexis_support: a pattern still undecided when it
+ * passes stops between two rounds with status FLEXIS_E_TIMEOUT.
  * Limits: one pattern per call, speculation window of 1024 roots, and the used-vertex bitmap
  * (n_vertices / 8 bytes) must fit the array beside about 96 KiB of other scratch, i.e. graphs of
  * up to about 66 million vertices; larger graphs return FLEXIS_E_UNSUPPORTED with the exact limit

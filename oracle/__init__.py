@@ -59,9 +59,6 @@ def lib():
                                      C.c_int64, C.POINTER(C.c_int64)]
             L.or_count_maps.restype = C.c_int64
             L.or_count_maps.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64]
-            L.or_plan.restype = C.c_int
-            L.or_plan.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, i32p,
-                                  C.POINTER(C.c_uint32), i32p]
             L.or_candidates.restype = C.c_int64
             L.or_candidates.argtypes = [C.c_int, i32p, i32p, i32p, i32p, C.c_int, i32p, i32p,
                                         u32p, C.c_int64]
@@ -180,21 +177,6 @@ class Graph:
     def count_maps(self, labels, edges, cap: int = 0) -> int:
         lab, m, e = _pat(labels, edges)
         return int(lib().or_count_maps(self._h, lab.size, lab, m, e, cap))
-
-    def plan(self, labels, edges):
-        """(rank labels in canonical order, code bits, matching order) or None if a label is
-        absent from the graph."""
-        lab, m, e = _pat(labels, edges)
-        n = lab.size
-        ol = np.zeros(n, np.int32)
-        opi = np.zeros(n, np.int32)
-        bits = C.c_uint32()
-        rc = lib().or_plan(self._h, n, lab, m, e, ol, C.byref(bits), opi)
-        if rc < 0:
-            raise ValueError("bad pattern")
-        if rc == 1:
-            return None
-        return tuple(int(x) for x in ol), int(bits.value), tuple(int(x) for x in opi)
 
     def mine(self, sigma: int, lam: float, max_edges: int):
         """Algorithm 1 with the predicate candidate generator.  Returns (patterns, levels) where

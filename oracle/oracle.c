@@ -32,7 +32,9 @@
  * Pins (tests/): the paper's running example (Fig. 1, Sec. 2.2, Sec. 2.4.4, Sec. 3.1.1), the
  * Theorem 1 tightness example (Fig. malVisual), brute-force agreement of the two tiers below,
  * Theorem 1 bounds against a brute-force maximum independent set, networkx isomorphism for the
- * canonical code, the candidate-generation figures (Sec. 3.2.1).  No function here is unpinned.
+ * canonical code, the candidate-generation figures (Sec. 3.2.1), and for the mining loop
+ * (Algorithm 1) a separate level-wise miner written in plain Python over brute-force maps.  No
+ * function here is unpinned.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -578,29 +580,6 @@ int64_t or_count_maps(void *gp, int n, const int32_t *labels, int m, const int32
         if (count_cap > 0 && total >= count_cap) break;
     }
     return total;
-}
-
-/* canonical plan as seen by the oracle: labels (rank space), adjacency bits (R2) and the
- * matching order (R3).  For tests that check the CUDA library's pattern compiler.              */
-int or_plan(void *gp, int n, const int32_t *labels, int m, const int32_t *edges, int32_t *out_lab,
-            uint32_t *out_bits, int32_t *out_pi)
-{
-    const or_graph *g = gp;
-    or_pat p;
-    if (pat_from(&p, n, labels, m, edges) || !pat_connected(&p)) return -1;
-    for (int i = 0; i < n; i++) {
-        int32_t r = (labels[i] >= 0 && labels[i] < g->nl) ? g->rank_of[labels[i]] : -1;
-        if (r < 0) return 1;
-        p.lab[i] = r;
-    }
-    or_pat q = canonical(&p, NULL);
-    int id[OR_MAXN], pi[OR_MAXN];
-    for (int i = 0; i < n; i++) id[i] = i;
-    or_code c = code_of(&q, id);
-    matching_order(&q, 0, pi);
-    for (int i = 0; i < n; i++) { out_lab[i] = c.lab[i]; out_pi[i] = pi[i]; }
-    *out_bits = c.bits;
-    return 0;
 }
 
 /* ------------------------------------------------------------------ candidate generation

@@ -98,6 +98,7 @@ _I64P = C.POINTER(C.c_int64)
 SYMBOLS = {
     "flexis_status_string": (C.c_char_p, [C.c_int]),
     "flexis_default_options": (None, [C.POINTER(flexis_options)]),
+    "flexis_lambda_quantize": (C.c_int, [C.c_double, _I64P]),
     "flexis_load_graph": (C.c_int, [C.c_int64, _I32P, C.c_int64, _I32P, _I32P,
                                      C.POINTER(flexis_options), C.POINTER(_P)]),
     "flexis_free_graph": (None, [_P]),
@@ -154,6 +155,13 @@ def lib():
                 f.argtypes = args
             _lib = L
     return _lib
+
+
+def lambda_quantize(lam: float) -> int:
+    """Numerator of lambda over LAMBDA_DEN, as the library quantises it (flexis_lambda_quantize)."""
+    q = C.c_int64()
+    _check(lib().flexis_lambda_quantize(float(lam), C.byref(q)), "flexis_lambda_quantize")
+    return int(q.value)
 
 
 def status_string(code: int) -> str:
@@ -270,7 +278,10 @@ class Graph:
         cnt = len(patterns)
         arr, keep = self._patterns(patterns)
         sig = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.int64), (cnt,)))
-        num = np.ascontiguousarray(np.rint(np.broadcast_to(np.asarray(lam, np.float64), (cnt,)) * LAMBDA_DEN).astype(np.int64))
+        lams = np.broadcast_to(np.asarray(lam, np.float64), (cnt,))
+        num = np.zeros(max(cnt, 1), np.int64)
+        for i in range(cnt):
+            num[i] = lambda_quantize(float(lams[i]))
         plans = np.zeros((max(1, cnt), 1024), np.uint8)
         rc = lib().flexis_compile(self._h, arr, sig.ctypes.data_as(_I64P), num.ctypes.data_as(_I64P),
                                   LAMBDA_DEN, cnt, mode, plans.ctypes.data_as(C.POINTER(flexis_plan)))

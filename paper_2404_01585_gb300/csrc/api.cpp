@@ -32,7 +32,7 @@ struct flexis_pattern_set {
 
 namespace {
 
-constexpr int64_t LAMBDA_DEN = 1000000;
+constexpr int64_t LAMBDA_DEN = FLEXIS_LAMBDA_DEN;
 
 bool lambda_to_q(double lambda, int64_t *num) {
     if (!(lambda >= 0.0 && lambda <= 1.0)) return false;  // also rejects NaN
@@ -165,6 +165,13 @@ const char *flexis_status_string(int status) {
     }
 }
 
+int flexis_lambda_quantize(double lambda, int64_t *num_out) {
+    int64_t num;
+    if (!num_out || !lambda_to_q(lambda, &num)) return FLEXIS_E_INVALID;
+    *num_out = num;
+    return FLEXIS_OK;
+}
+
 void flexis_default_options(flexis_options *opt) {
     if (!opt) return;
     memset(opt, 0, sizeof *opt);
@@ -292,7 +299,8 @@ void *flexis_graph_stream(const flexis_graph *g) { return g ? (void *)dev_graph_
 int flexis_support_noalloc(flexis_graph *g, const flexis_plan *plan, flexis_support_result *out,
                            void *stream) {
     if (!g || !plan || !out) return FLEXIS_E_INVALID;
-    return dev_support_noalloc(g->dg, reinterpret_cast<const Plan *>(plan), out, (cudaStream_t)stream);
+    return dev_support_noalloc(g->dg, reinterpret_cast<const Plan *>(plan), out, (cudaStream_t)stream,
+                               g->opt.deadline_ms);
 }
 
 int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,

@@ -48,7 +48,7 @@ int dev_pattern_bytes(const DeviceGraph *g, int32_t Wmax, int32_t sel, int64_t *
 
 // One pattern evaluated with device scratch taken from a static device array (no allocation).
 int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_result *h_out,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int32_t deadline_ms);
 int64_t noalloc_max_vertices();
 int dev_free_bytes(const DeviceGraph *g, int64_t *bytes);
 

@@ -1693,7 +1693,8 @@ static int noalloc_base(int device, unsigned char **out) {
 }
 
 int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_result *h_out,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int32_t deadline_ms) {
+    const auto t_start = std::chrono::steady_clock::now();
     CK(cudaSetDevice(g->device));
     const NoallocLayout L = noalloc_layout(g->view.words);
     if (L.end > NOALLOC_SCRATCH_BYTES) {
@@ -1744,6 +1745,13 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
         CK(cudaMemcpyAsync(&h_ctl, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         if (h_ctl.active[(round - 1) & 1] == 0) break;
+        // the graph's deadline, checked between pairs of rounds as in dev_eval: an undecided
+        // pattern stops with FLEXIS_E_TIMEOUT
+        if (deadline_ms > 0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count() > deadline_ms) {
+            k_cancel<<<1, 32, 0, stream>>>(B, nullptr, 1);
+            break;
+        }
     }
     k_mni_setup<<<1, 1024, 0, stream>>>(B);
     k_mni<<<sblocks, SEARCH_THREADS, 0, stream>>>(B);

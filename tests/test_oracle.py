@@ -492,3 +492,37 @@ def test_mining_levels_consistent():
         assert mis >= max(tau, 1) and mni >= mis
     for k, (cand, freq) in levels.items():
         assert freq == sum(1 for p in pats if p[0] == k) and freq <= cand
+
+
+def mining_cases(count, seed):
+    st = Stream(seed)
+    out = []
+    for _ in range(count):
+        nv = 8 + int(st.integers(1, 5)[0])             # 8..12 vertices
+        ne = nv + int(st.integers(1, nv)[0])           # nv .. 2nv - 1 edges
+        nl = 1 + int(st.integers(1, 3)[0])             # 1..3 labels
+        s = int(st.next(1)[0] % (1 << 31))
+        src, dst = erdos_renyi(nv, ne, s)
+        lab = labels_uniform(nv, nl, s + 1)
+        sigma = 1 + int(st.integers(1, 4)[0])          # 1..4
+        lam = (0.0, 0.5, 1.0)[int(st.integers(1, 3)[0])]
+        max_edges = 2 + int(st.integers(1, 3)[0])      # 2..4
+        out.append((lab, src, dst, sigma, lam, max_edges, s))
+    return out
+
+
+def test_mining_matches_python_level_wise_miner():
+    # Algorithm 1 restated in plain Python over brute-force maps (tests/bruteforce.py): the
+    # whole frequent set (codes, tau, mis, mni) and the per-level candidate and frequent counts
+    # must be identical.  Seeds vary the greedy order; levels with infrequent candidates make
+    # generating from C_k instead of F_k visible, and every level-2 label pair matters.
+    saw_infrequent = 0
+    for lab, src, dst, sigma, lam, max_edges, s in mining_cases(30, 2024):
+        E = list(zip(src.tolist(), dst.tolist()))
+        want, wlev = bf.mine(lab.tolist(), E, sigma, int(round(lam * 10**6)), 10**6, max_edges, seed=s)
+        g = oracle.Graph(lab, src, dst, seed=s)
+        got, glev = g.mine(sigma=sigma, lam=lam, max_edges=max_edges)
+        assert glev == wlev, (sigma, lam, max_edges, glev, wlev)
+        assert got == want, (sigma, lam, max_edges)
+        saw_infrequent += sum(1 for c, f in wlev.values() if f < c)
+    assert saw_infrequent >= 10
