@@ -65,11 +65,32 @@ extern "C" {
 #define FLEXIS_MODE_NO_MNI 4 /* or-ed into a mode: skip the MNI count (mni = -1).  The paper's
                                 metric step (Sec. 3.2.2) computes the mIS only; mining uses
                                 FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI */
+#define FLEXIS_MODE_COUNT_MAPS 8 /* or-ed into a mode: also count the set of maps M (Sec. 2.4) into
+                                    n_maps, by a level-by-level enumeration of all maps (not only
+                                    the greedy's first map per root); saturates at
+                                    options.maps_cap (FLEXIS_FLAG_MAPS_SATURATED) */
+#define FLEXIS_MODE_NO_MIS 16 /* or-ed into a mode: skip the greedy mIS phase (mis = -1,
+                                 frequent = 0, FLEXIS_FLAG_MIS_SKIPPED).  With
+                                 FLEXIS_MODE_COUNT_MAPS | FLEXIS_MODE_FULL this is the count-only
+                                 mode: |M| and the exact MNI (Sec. 2.4.4) without the greedy */
+#define FLEXIS_MODE_EXACT_MIS 32 /* or-ed into a mode: also compute the maximum independent set of
+                                    the overlap graph (MIS, Sec. 2.4.2) into mis_exact, for small
+                                    overlap graphs: all maps are materialised, reduced to distinct
+                                    instances (image vertex sets), conflict edges are built from a
+                                    vertex -> instance index, and a branch-and-bound search runs on
+                                    the device.  Beyond options.exact_mis_maps instances or
+                                    options.exact_mis_nodes search nodes the result is a lower
+                                    bound flagged FLEXIS_FLAG_EXACT_MIS_SATURATED */
 
 /* result flags */
 #define FLEXIS_FLAG_ABSENT_LABEL 1u /* a pattern label does not occur in the data graph */
 #define FLEXIS_FLAG_MNI_FROM_MIS 2u /* mni follows from mis (mis reached c, or M is empty) */
 #define FLEXIS_FLAG_MNI_SKIPPED 4u  /* FLEXIS_MODE_NO_MNI: mni not computed (-1) */
+#define FLEXIS_FLAG_MIS_SATURATED 8u  /* EARLY: mis reached c; the pattern's mIS may be larger */
+#define FLEXIS_FLAG_MNI_SATURATED 16u /* EARLY: mni reached c; the pattern's MNI may be larger */
+#define FLEXIS_FLAG_MAPS_SATURATED 32u /* n_maps reached options.maps_cap; |M| may be larger */
+#define FLEXIS_FLAG_MIS_SKIPPED 64u   /* FLEXIS_MODE_NO_MIS: the greedy phase did not run */
+#define FLEXIS_FLAG_EXACT_MIS_SATURATED 128u /* mis_exact is a lower bound (instance or node limit) */
 
 #define FLEXIS_MAX_PATTERN 8 /* largest pattern, in vertices */
 
@@ -108,7 +129,16 @@ typedef struct {
                                 1 = interpolation search guarded by bisection, with the candidate's
                                 used-bit and vertex-record loads issued together.  Results are
                                 identical; 1 is checked on the host and not yet timed on a GPU */
-    int32_t reserved[1];
+    int32_t directed;        /* 0 = undirected data graph (each edge read both ways, the paper's
+                                loader, Sec. 4.1); 1 = directed: (src[e], dst[e]) is one arc and
+                                pattern edges are arcs too (the paper's directed matcher, Sec. 2.2) */
+    int64_t maps_cap;        /* FLEXIS_MODE_COUNT_MAPS: n_maps saturates here (0 = 2^32) */
+    int64_t frontier_rows;   /* rows of one level of the map enumerator's frontier (0 = 2^22);
+                                raised to at least the largest vertex degree */
+    int64_t exact_mis_nodes; /* FLEXIS_MODE_EXACT_MIS: branch-and-bound nodes per pattern (0 = 2^24) */
+    int32_t exact_mis_maps;  /* FLEXIS_MODE_EXACT_MIS: largest number of distinct instances whose
+                                overlap graph is searched (0 = 2048, at most 4096) */
+    int32_t reserved[5];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
@@ -132,6 +162,10 @@ typedef struct {
     int64_t mni;      /* minimum image count (capped in EARLY mode) */
     int32_t frequent; /* mis >= max(tau, 1) */
     uint32_t flags;   /* FLEXIS_FLAG_* */
+    uint64_t n_maps;  /* FLEXIS_MODE_COUNT_MAPS: |M|, the number of maps (Sec. 2.4; automorphic
+                         maps counted separately), saturating at options.maps_cap; else 0 */
+    int64_t mis_exact;/* FLEXIS_MODE_EXACT_MIS: size of a maximum independent set of the maps
+                         (Sec. 2.4.2); else -1 */
     int64_t roots_searched; /* diagnostics below: not part of the result                      */
                             /* root searches run by the greedy phase                          */
     int64_t search_steps;   /* candidate chunks scanned by those searches                     */
@@ -180,6 +214,10 @@ typedef struct {
     int32_t batches;          /* device batches (memory-admitted chunks of the patterns) */
     int32_t graph_launches;   /* replays of the captured round-loop CUDA graph (each runs the
                                  rounds between two host checks); 0 when launched one by one */
+    int64_t enum_rows;        /* map enumerator (FLEXIS_MODE_COUNT_MAPS / _EXACT_MIS): partial
+                                 maps extended */
+    int64_t enum_scanned;     /* ... label-slice entries scanned by those extensions */
+    int64_t enum_bytes;       /* ... algorithmic bytes read by them */
 } flexis_stats;
 
 const char *flexis_status_string(int status);
@@ -260,6 +298,21 @@ int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int
  * serialise them.                                                                               */
 int flexis_support_noalloc(flexis_graph *g, const flexis_plan *plan, flexis_support_result *out,
                            void *stream);
+
+/* Overlap graph of one pattern (Sec. 2.4.1: two maps overlap when they share a data vertex),
+ * built on the device as for FLEXIS_MODE_EXACT_MIS: every map is enumerated, maps with the same
+ * image vertex set are merged into one instance, a data-vertex -> instance index is built by
+ * sorting (vertex, instance) keys, and each vertex's run of instances gives conflict edges.
+ *   instances_out : cap_instances rows of 8 ids (an instance's vertices ascending, -1 padded),
+ *                   rows in ascending lexicographic order; *n_instances = their number
+ *   edges_out     : cap_edges pairs (a, b), a < b, instance indices whose vertex sets meet, in
+ *                   ascending order; *n_edges = their number
+ * At most cap_* entries are written (the counts are complete).  FLEXIS_E_UNSUPPORTED (with
+ * *n_instances = -1) when the pattern has more maps or instances than the limits of
+ * FLEXIS_MODE_EXACT_MIS (options.exact_mis_maps).  A label absent from the graph gives 0 / 0. */
+int flexis_overlap_graph(flexis_graph *g, const flexis_pattern *pattern, int32_t *instances_out,
+                         int64_t cap_instances, int64_t *n_instances, int32_t *edges_out,
+                         int64_t cap_edges, int64_t *n_edges);
 
 /* Counters of the last evaluation call on g. */
 int flexis_last_stats(const flexis_graph *g, flexis_stats *out);

@@ -59,6 +59,13 @@ def lib():
                                      C.c_int64, C.POINTER(C.c_int64)]
             L.or_count_maps.restype = C.c_int64
             L.or_count_maps.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64]
+            L.or_overlap_graph.restype = C.c_int
+            L.or_overlap_graph.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64, i32p,
+                                           C.c_int64, C.POINTER(C.c_int64), i32p, C.c_int64,
+                                           C.POINTER(C.c_int64)]
+            L.or_max_independent_set.restype = C.c_int64
+            L.or_max_independent_set.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64,
+                                                 C.c_int64]
             L.or_candidates.restype = C.c_int64
             L.or_candidates.argtypes = [C.c_int, i32p, i32p, i32p, i32p, C.c_int, i32p, i32p,
                                         u32p, C.c_int64]
@@ -177,6 +184,34 @@ class Graph:
     def count_maps(self, labels, edges, cap: int = 0) -> int:
         lab, m, e = _pat(labels, edges)
         return int(lib().or_count_maps(self._h, lab.size, lab, m, e, cap))
+
+    def overlap_graph(self, labels, edges, max_maps: int = 1 << 20, cap_inst: int = 1 << 14,
+                      cap_edges: int = 1 << 22):
+        """(instances, conflict edges): instances = sorted list of sorted image vertex tuples,
+        edges = sorted list of (a, b), a < b, instance indices whose vertex sets meet.  None if
+        the maps or instances exceed the limits."""
+        lab, m, e = _pat(labels, edges)
+        n = lab.size
+        inst = np.zeros((cap_inst, 8), np.int32)
+        ed = np.zeros((cap_edges, 2), np.int32)
+        ni, ne = C.c_int64(), C.c_int64()
+        rc = lib().or_overlap_graph(self._h, n, lab, m, e, max_maps, inst.reshape(-1), cap_inst,
+                                    C.byref(ni), ed.reshape(-1), cap_edges, C.byref(ne))
+        if rc == -1:
+            raise ValueError("bad pattern")
+        if rc == -2:
+            return None
+        return ([tuple(int(x) for x in inst[i, :n]) for i in range(ni.value)],
+                [(int(ed[i, 0]), int(ed[i, 1])) for i in range(ne.value)])
+
+    def max_independent_set(self, labels, edges, max_maps: int = 1 << 20, max_inst: int = 64):
+        """Size of a maximum independent set of the maps (Sec. 2.4.2), or None beyond the limits
+        (the search is exhaustive)."""
+        lab, m, e = _pat(labels, edges)
+        r = int(lib().or_max_independent_set(self._h, lab.size, lab, m, e, max_maps, max_inst))
+        if r == -1:
+            raise ValueError("bad pattern")
+        return None if r == -2 else r
 
     def mine(self, sigma: int, lam: float, max_edges: int):
         """Algorithm 1 with the predicate candidate generator.  Returns (patterns, levels) where

@@ -582,6 +582,150 @@ int64_t or_count_maps(void *gp, int n, const int32_t *labels, int m, const int32
     return total;
 }
 
+/* ------------------------------------------------------------------ overlap graph and MIS
+ * Sec. 2.4.1: two maps overlap when they share a data vertex.  Maps with the same image vertex
+ * set (an "instance") overlap each other and every other map the same way, so a maximum
+ * independent set of maps (Sec. 2.4.2) has the size of a maximum independent set of distinct
+ * instances.  The oracle lists every map (tier-1 backtracking, no used set), sorts each map's
+ * image ascending, sorts and deduplicates the instances, and joins two instances by a conflict
+ * edge when their vertex sets intersect (plain pairwise test).                                 */
+static int cmp_inst(const void *a, const void *b)
+{
+    const int32_t *x = a, *y = b;
+    for (int i = 0; i < OR_MAXN; i++)
+        if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+    return 0;
+}
+
+/* instances (sorted rows of 8 ids, -1 padded) of a pattern; returns their number, -1 on a bad
+ * pattern, or -2 if the pattern has more than max_maps maps.  *out is malloc'ed.               */
+static int64_t instances_of(const or_graph *g, int n, const int32_t *labels, int m, const int32_t *edges,
+                            int64_t max_maps, int32_t **out)
+{
+    *out = NULL;
+    or_pat p;
+    if (n < 2 || pat_from(&p, n, labels, m, edges) || !pat_connected(&p)) return -1;
+    for (int i = 0; i < n; i++) {
+        int32_t r = (labels[i] >= 0 && labels[i] < g->nl) ? g->rank_of[labels[i]] : -1;
+        if (r < 0) return 0;
+        p.lab[i] = r;
+    }
+    or_pat q = canonical(&p, NULL);
+    int pi[OR_MAXN];
+    matching_order(&q, 0, pi);
+    map_list M = {0};
+    for (int64_t r = 0; r < g->nv; r++) {
+        if (g->lab[r] != q.lab[pi[0]]) continue;
+        bt_state s;
+        memset(&s, 0, sizeof s);
+        s.g = g; s.q = &q; s.pi = pi; s.out = &M;
+        s.e[pi[0]] = (int32_t)r;
+        bt_level(&s, 1);
+        if (M.len > max_maps) { free(M.a); return -2; }
+    }
+    int32_t *rows = malloc((M.len > 0 ? M.len : 1) * OR_MAXN * sizeof *rows);
+    for (int64_t t = 0; t < M.len; t++) {
+        int32_t *row = rows + OR_MAXN * t;
+        for (int i = 0; i < OR_MAXN; i++) row[i] = i < n ? M.a[t].v[i] : -1;
+        /* insertion sort of the n image vertices */
+        for (int i = 1; i < n; i++)
+            for (int k = i; k > 0 && row[k - 1] > row[k]; k--) { int32_t x = row[k]; row[k] = row[k - 1]; row[k - 1] = x; }
+    }
+    free(M.a);
+    qsort(rows, (size_t)M.len, OR_MAXN * sizeof *rows, cmp_inst);
+    int64_t k = 0;
+    for (int64_t t = 0; t < M.len; t++)
+        if (k == 0 || cmp_inst(rows + OR_MAXN * t, rows + OR_MAXN * (k - 1)) != 0) {
+            if (k != t) memcpy(rows + OR_MAXN * k, rows + OR_MAXN * t, OR_MAXN * sizeof *rows);
+            k++;
+        }
+    *out = rows;
+    return k;
+}
+
+static int inst_meet(const int32_t *a, const int32_t *b, int n)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) if (a[i] == b[j]) return 1;
+    return 0;
+}
+
+/* exported: the overlap graph of a pattern's instances.  inst_out[cap_inst * 8] (sorted,
+ * -1 padded rows, in ascending order), *n_inst; edges_out[2 * cap_edges] pairs a < b in
+ * lexicographic order, *n_edges.  Returns 0, -1 on a bad pattern, -2 if the maps exceed
+ * max_maps or the instances / edges exceed their capacities.                                  */
+int or_overlap_graph(void *gp, int n, const int32_t *labels, int m, const int32_t *edges, int64_t max_maps,
+                     int32_t *inst_out, int64_t cap_inst, int64_t *n_inst, int32_t *edges_out,
+                     int64_t cap_edges, int64_t *n_edges)
+{
+    int32_t *rows;
+    int64_t k = instances_of(gp, n, labels, m, edges, max_maps, &rows);
+    *n_inst = k > 0 ? k : 0;
+    *n_edges = 0;
+    if (k < 0) { free(rows); return (int)k; }
+    if (k > cap_inst) { free(rows); return -2; }
+    if (k > 0) memcpy(inst_out, rows, (size_t)k * OR_MAXN * sizeof *rows);
+    int64_t e = 0;
+    for (int64_t a = 0; a < k; a++)
+        for (int64_t b = a + 1; b < k; b++)
+            if (inst_meet(rows + OR_MAXN * a, rows + OR_MAXN * b, n)) {
+                if (e >= cap_edges) { free(rows); return -2; }
+                edges_out[2 * e] = (int32_t)a;
+                edges_out[2 * e + 1] = (int32_t)b;
+                e++;
+            }
+    *n_edges = e;
+    free(rows);
+    return 0;
+}
+
+/* maximum independent set of the instances (Sec. 2.4.2) by exhaustive search: each instance is
+ * either taken (if it meets no taken one) or left out; a branch stops when even taking every
+ * remaining instance could not beat the best set found.                                        */
+typedef struct {
+    const int32_t *rows;
+    int n;
+    int64_t k;
+    uint8_t *conf;   /* k x k conflict matrix */
+    int64_t best;
+} mis_state;
+
+static void mis_rec(mis_state *s, int64_t i, int64_t size, uint8_t *taken)
+{
+    if (size + (s->k - i) <= s->best) return;
+    if (i == s->k) { s->best = size; return; }
+    int ok = 1;
+    for (int64_t j = 0; j < i && ok; j++)
+        if (taken[j] && s->conf[i * s->k + j]) ok = 0;
+    if (ok) {
+        taken[i] = 1;
+        mis_rec(s, i + 1, size + 1, taken);
+        taken[i] = 0;
+    }
+    mis_rec(s, i + 1, size, taken);
+}
+
+/* exported: size of a maximum independent set of the pattern's maps; -1 on a bad pattern, -2 if
+ * the maps exceed max_maps or the instances exceed max_inst.                                   */
+int64_t or_max_independent_set(void *gp, int n, const int32_t *labels, int m, const int32_t *edges,
+                               int64_t max_maps, int64_t max_inst)
+{
+    int32_t *rows;
+    int64_t k = instances_of(gp, n, labels, m, edges, max_maps, &rows);
+    if (k < 0) { free(rows); return k; }
+    if (k > max_inst) { free(rows); return -2; }
+    mis_state s;
+    s.rows = rows; s.n = n; s.k = k; s.best = 0;
+    s.conf = calloc((size_t)(k > 0 ? k * k : 1), 1);
+    for (int64_t a = 0; a < k; a++)
+        for (int64_t b = 0; b < k; b++)
+            s.conf[a * k + b] = (uint8_t)(a != b && inst_meet(rows + OR_MAXN * a, rows + OR_MAXN * b, n));
+    uint8_t *taken = calloc((size_t)(k > 0 ? k : 1), 1);
+    mis_rec(&s, 0, 0, taken);
+    free(taken); free(s.conf); free(rows);
+    return s.best;
+}
+
 /* ------------------------------------------------------------------ candidate generation
  * Predicate form of Algorithms 2-4 (Sec. 3.2.1).  With F = the frequent (k-1)-vertex patterns,
  * a connected k-vertex pattern P is a candidate iff

@@ -29,9 +29,17 @@ FLEXIS_E_BUSY = -7
 FLEXIS_MODE_FULL = 0
 FLEXIS_MODE_EARLY = 1
 FLEXIS_MODE_NO_MNI = 4
+FLEXIS_MODE_COUNT_MAPS = 8
+FLEXIS_MODE_NO_MIS = 16
+FLEXIS_MODE_EXACT_MIS = 32
 FLEXIS_FLAG_ABSENT_LABEL = 1
 FLEXIS_FLAG_MNI_FROM_MIS = 2
 FLEXIS_FLAG_MNI_SKIPPED = 4
+FLEXIS_FLAG_MIS_SATURATED = 8
+FLEXIS_FLAG_MNI_SATURATED = 16
+FLEXIS_FLAG_MAPS_SATURATED = 32
+FLEXIS_FLAG_MIS_SKIPPED = 64
+FLEXIS_FLAG_EXACT_MIS_SATURATED = 128
 LAMBDA_DEN = 1_000_000
 DEFAULT_SEED = 0x5EED
 
@@ -48,7 +56,9 @@ class flexis_options(C.Structure):
                 ("record_selected", C.c_int32), ("search_budget", C.c_int32),
                 ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("timing", C.c_int32),
                 ("graphs", C.c_int32), ("deadline_ms", C.c_int32), ("root_order", C.c_int32),
-                ("search_variant", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("search_variant", C.c_int32), ("directed", C.c_int32), ("maps_cap", C.c_int64),
+                ("frontier_rows", C.c_int64), ("exact_mis_nodes", C.c_int64),
+                ("exact_mis_maps", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class flexis_pattern(C.Structure):
@@ -59,14 +69,22 @@ class flexis_pattern(C.Structure):
 class flexis_support_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("sigma", C.c_int64), ("tau", C.c_int64),
                 ("cap", C.c_int64), ("mis", C.c_int64), ("mni", C.c_int64),
-                ("frequent", C.c_int32), ("flags", C.c_uint32), ("roots_searched", C.c_int64),
+                ("frequent", C.c_int32), ("flags", C.c_uint32), ("n_maps", C.c_uint64),
+                ("mis_exact", C.c_int64), ("roots_searched", C.c_int64),
                 ("search_steps", C.c_int64), ("max_item_steps", C.c_int32), ("rounds", C.c_int32)]
 
     def as_dict(self):
         return dict(status=self.status, n=self.n, sigma=self.sigma, tau=self.tau, cap=self.cap,
                     mis=self.mis, mni=self.mni, frequent=bool(self.frequent), flags=self.flags,
+                    n_maps=self.n_maps, mis_exact=self.mis_exact,
                     roots_searched=self.roots_searched, search_steps=self.search_steps,
                     max_item_steps=self.max_item_steps, rounds=self.rounds)
+
+
+RESULT_DTYPE = np.dtype([("status", "<i4"), ("n", "<i4"), ("sigma", "<i8"), ("tau", "<i8"),
+                         ("cap", "<i8"), ("mis", "<i8"), ("mni", "<i8"), ("frequent", "<i4"),
+                         ("flags", "<u4"), ("n_maps", "<u8"), ("mis_exact", "<i8"), ("roots", "<i8"),
+                         ("steps", "<i8"), ("maxsteps", "<i4"), ("rounds", "<i4")])
 
 
 class flexis_plan(C.Structure):
@@ -85,7 +103,8 @@ class flexis_stats(C.Structure):
                 ("alg_bytes_greedy", C.c_int64), ("patterns", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
                 ("total_ms", C.c_float), ("host_gen_ms", C.c_float), ("host_compile_ms", C.c_float),
-                ("search_launches", C.c_int32), ("batches", C.c_int32), ("graph_launches", C.c_int32)]
+                ("search_launches", C.c_int32), ("batches", C.c_int32), ("graph_launches", C.c_int32),
+                ("enum_rows", C.c_int64), ("enum_scanned", C.c_int64), ("enum_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,6 +135,8 @@ SYMBOLS = {
     "flexis_graph_stream": (C.c_void_p, [_P]),
     "flexis_support_noalloc": (C.c_int, [_P, C.POINTER(flexis_plan), C.POINTER(flexis_support_result), _P]),
     "flexis_selected_maps": (C.c_int, [_P, C.c_int32, _I32P, C.c_int64, _I64P]),
+    "flexis_overlap_graph": (C.c_int, [_P, C.POINTER(flexis_pattern), _I32P, C.c_int64, _I64P, _I32P,
+                                        C.c_int64, _I64P]),
     "flexis_mine": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int32, C.POINTER(_P)]),
     "flexis_pattern_set_count": (C.c_int64, [_P]),
     "flexis_pattern_set_get": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P, _I32P, _I32P,
@@ -202,7 +223,8 @@ class Graph:
 
     Keyword options are the fields of flexis_options: seed, device, window_min, window_max,
     search_blocks, record_selected, search_budget, split_pieces, sub_searches, timing, graphs,
-    deadline_ms, root_order, search_variant (meanings in include/flexis.h).  They apply to every
+    deadline_ms, root_order, search_variant, directed, maps_cap, frontier_rows, exact_mis_nodes,
+    exact_mis_maps (meanings in include/flexis.h).  They apply to every
     call on the graph and to servers started on it."""
 
     def __init__(self, labels, src, dst, **options):
@@ -319,6 +341,21 @@ class Graph:
                "flexis_selected_maps")
         return [tuple(int(x) for x in buf[j, :n]) for j in range(k.value)]
 
+    def overlap_graph(self, labels, edges, cap_instances=1 << 12, cap_edges=1 << 22):
+        """flexis_overlap_graph: (instances, conflict edges), instances as sorted vertex tuples
+        in ascending order, edges as (a, b) pairs, a < b, ascending."""
+        p, keep = make_pattern(labels, edges)
+        inst = np.zeros((max(cap_instances, 1), 8), np.int32)
+        ed = np.zeros((max(cap_edges, 1), 2), np.int32)
+        ni, ne = C.c_int64(), C.c_int64()
+        _check(lib().flexis_overlap_graph(self._h, C.byref(p), inst.ctypes.data_as(_I32P), cap_instances,
+                                          C.byref(ni), ed.ctypes.data_as(_I32P), cap_edges, C.byref(ne)),
+               "flexis_overlap_graph")
+        n = p.n
+        k = min(ni.value, cap_instances)
+        return ([tuple(int(x) for x in inst[i, :n]) for i in range(k)],
+                [(int(ed[i, 0]), int(ed[i, 1])) for i in range(min(ne.value, cap_edges))])
+
     def mine(self, sigma, lam, max_edges):
         """Algorithm 1.  Returns (patterns, levels): patterns = list of dict(n, labels, edges,
         code_labels, code_bits, tau, mis, mni) sorted by (n, canonical code); levels maps
@@ -360,11 +397,7 @@ class Graph:
                                             lab.ctypes.data_as(_I32P), res)
             if got != cnt:
                 raise FlexisError(FLEXIS_E_INVALID, "flexis_pattern_set_read")
-            rr = np.frombuffer(res, dtype=np.dtype([("status", "<i4"), ("n", "<i4"), ("sigma", "<i8"),
-                                                   ("tau", "<i8"), ("cap", "<i8"), ("mis", "<i8"),
-                                                   ("mni", "<i8"), ("frequent", "<i4"), ("flags", "<u4"),
-                                                   ("roots", "<i8"), ("steps", "<i8"), ("maxsteps", "<i4"),
-                                                   ("rounds", "<i4")]), count=cnt)
+            rr = np.frombuffer(res, dtype=RESULT_DTYPE, count=cnt)
             cand = np.zeros(9, np.int64)
             freq = np.zeros(9, np.int64)
             L.flexis_pattern_set_levels(h, cand.ctypes.data_as(_I64P), freq.ctypes.data_as(_I64P))

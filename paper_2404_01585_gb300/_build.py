@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflexis.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["kernels.cu", "graph.cpp", "pattern.cpp", "api.cpp"]
+SOURCES = ["kernels.cu", "enumerate.cu", "graph.cpp", "pattern.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def _deps():
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(INCLUDE, "flexis.h"))
     return max(os.path.getmtime(h) for h in hdrs)
 

@@ -77,6 +77,9 @@ void add_stats(flexis_stats &a, const flexis_stats &b) {
     a.search_launches += b.search_launches;
     a.batches += b.batches;
     a.graph_launches += b.graph_launches;
+    a.enum_rows += b.enum_rows;
+    a.enum_scanned += b.enum_scanned;
+    a.enum_bytes += b.enum_bytes;
 }
 
 // Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism
@@ -107,20 +110,42 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     return c;
 }
 
+// Map enumerator settings of a set of plans: which passes run, and their limits.
+constexpr int32_t EXACT_MIS_DEFAULT_INSTANCES = 2048, EXACT_MIS_MAX_INSTANCES = 4096;
+constexpr int32_t EXACT_MIS_BATCH = 64;  // patterns whose maps are materialised at once
+
+void enum_config(const flexis_graph *g, const Plan *plans, int64_t n, EvalConfig &c) {
+    c.count_maps = c.exact_mis = false;
+    for (int64_t i = 0; i < n; i++) {
+        c.count_maps |= plans[i].count_maps != 0;
+        c.exact_mis |= plans[i].exact_mis != 0;
+    }
+    c.maps_cap = g->opt.maps_cap;
+    c.frontier_rows = g->opt.frontier_rows;
+    c.exact_mis_maps = g->opt.exact_mis_maps > 0 ? std::min(g->opt.exact_mis_maps, EXACT_MIS_MAX_INSTANCES)
+                                                 : EXACT_MIS_DEFAULT_INSTANCES;
+    c.exact_mis_maps_buffer = std::min(65536, 32 * c.exact_mis_maps);
+    c.exact_mis_nodes = g->opt.exact_mis_nodes;
+}
+
 // Memory-admitted batches: the device workspace of one batch (used bitmaps, windows, items) is
 // bounded by a share of the free device memory; larger candidate sets run as several batches.
 int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result *out) {
     const int64_t P = (int64_t)plans.size();
     EvalConfig cfg = config_for(g, (int32_t)std::min<int64_t>(P, INT32_MAX));
+    enum_config(g, plans.data(), P, cfg);
     int64_t per = 1, fr = 0;
     dev_pattern_bytes(g->dg, cfg.w_max, cfg.record_selected, &per);
     dev_free_bytes(g->dg, &fr);
     const int64_t budget = std::max<int64_t>(fr / 3, 256ll << 20);
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({P, budget / std::max<int64_t>(per, 1), 1 << 22}));
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({P, budget / std::max<int64_t>(per, 1), 1 << 22}));
+    // the exact MIS materialises every map of its patterns: a few patterns at a time
+    if (cfg.exact_mis) chunk = std::min<int64_t>(chunk, EXACT_MIS_BATCH);
     flexis_stats total{};
     for (int64_t lo = 0; lo < P; lo += chunk) {
         const int32_t cnt = (int32_t)std::min(chunk, P - lo);
         EvalConfig c2 = config_for(g, cnt);
+        enum_config(g, plans.data() + lo, cnt, c2);
         flexis_stats st{};
         int rc = dev_eval_host(g->dg, plans.data() + lo, cnt, out + lo, c2, &st);
         if (rc) return rc;
@@ -285,6 +310,14 @@ int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int
     if (!g || count < 0 || (count > 0 && (!d_plans || !d_results))) return FLEXIS_E_INVALID;
     EvalConfig cfg = config_for(g, count);
     cudaStream_t s = stream ? (cudaStream_t)stream : dev_graph_stream(g->dg);
+    if (count > 0) {
+        // the plans' mode flags decide which enumerator passes run: read them back (1 KB each)
+        std::vector<Plan> h((size_t)count);
+        if (cudaMemcpyAsync(h.data(), d_plans, sizeof(Plan) * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return FLEXIS_E_CUDA;
+        enum_config(g, h.data(), count, cfg);
+    }
     return dev_eval(g->dg, reinterpret_cast<const Plan *>(d_plans), count, d_results, s, cfg, &g->last);
 }
 
@@ -301,6 +334,26 @@ int flexis_support_noalloc(flexis_graph *g, const flexis_plan *plan, flexis_supp
     if (!g || !plan || !out) return FLEXIS_E_INVALID;
     return dev_support_noalloc(g->dg, reinterpret_cast<const Plan *>(plan), out, (cudaStream_t)stream,
                                g->opt.deadline_ms);
+}
+
+int flexis_overlap_graph(flexis_graph *g, const flexis_pattern *pattern, int32_t *instances_out,
+                         int64_t cap_instances, int64_t *n_instances, int32_t *edges_out, int64_t cap_edges,
+                         int64_t *n_edges) {
+    if (!g || !pattern || !n_instances || !n_edges || cap_instances < 0 || cap_edges < 0 ||
+        (cap_instances > 0 && !instances_out) || (cap_edges > 0 && !edges_out))
+        return FLEXIS_E_INVALID;
+    std::vector<Plan> plans(1);
+    int rc = compile_plan(g->hg, *pattern, 1, 0, 1,
+                          FLEXIS_MODE_FULL | FLEXIS_MODE_NO_MNI | FLEXIS_MODE_NO_MIS | FLEXIS_MODE_EXACT_MIS, plans[0]);
+    if (rc) return rc;
+    flexis_support_result r;
+    if ((rc = eval_plans(g, plans, &r))) return rc;
+    if (plans[0].flags & FLEXIS_FLAG_ABSENT_LABEL) {
+        *n_instances = 0;
+        *n_edges = 0;
+        return FLEXIS_OK;
+    }
+    return dev_overlap_read(g->dg, 0, instances_out, cap_instances, n_instances, edges_out, cap_edges, n_edges);
 }
 
 int flexis_selected_maps(const flexis_graph *g, int32_t i, int32_t *maps_out, int64_t cap,

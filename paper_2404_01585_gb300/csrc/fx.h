@@ -46,6 +46,10 @@ struct Plan {
     int32_t want_mni;               // 0 under FLEXIS_MODE_NO_MNI
     int32_t lab_begin[MAXN], lab_end[MAXN];  // label-index slice of each canonical vertex's label
     uint64_t need[MAXN];            // rank labels (< 64) of each canonical vertex's neighbours
+    int32_t count_maps;             // FLEXIS_MODE_COUNT_MAPS: enumerate and count all maps
+    int32_t skip_mis;               // FLEXIS_MODE_NO_MIS: no greedy phase
+    int32_t exact_mis;              // FLEXIS_MODE_EXACT_MIS: maximum independent set of the instances
+    int32_t pad_;
 };
 static_assert(sizeof(Plan) <= sizeof(flexis_plan), "plan must fit flexis_plan");
 

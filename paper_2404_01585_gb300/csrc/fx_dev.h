@@ -21,6 +21,13 @@ struct EvalConfig {
     bool graphs = true;         // replay the round loop as a captured CUDA graph
     int32_t deadline_ms = 0;    // > 0: patterns undecided after this long stop with FLEXIS_E_TIMEOUT
     int32_t search_variant = 0; // 1: interpolation-search membership tests (see search_util.h)
+    bool count_maps = false;    // some plan wants n_maps (or may: plans already on the device)
+    bool exact_mis = false;     // some plan wants the exact MIS
+    int64_t maps_cap = 0;       // n_maps saturation (0: default)
+    int64_t frontier_rows = 0;  // rows per frontier level of the map enumerator (0: default)
+    int32_t exact_mis_maps = 0;         // instance limit of the exact MIS (0: default)
+    int32_t exact_mis_maps_buffer = 0;  // maps materialised per pattern for it
+    int64_t exact_mis_nodes = 0;        // branch-and-bound node budget (0: default)
 };
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);
@@ -51,6 +58,12 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
                         cudaStream_t stream, int32_t deadline_ms);
 int64_t noalloc_max_vertices();
 int dev_free_bytes(const DeviceGraph *g, int64_t *bytes);
+
+// Overlap graph of pattern p of the last evaluation with FLEXIS_MODE_EXACT_MIS: its instances
+// (sorted rows of MAXN ids, -1 padded, ascending) and conflict edges (a < b, ascending).  Writes
+// at most cap_inst rows / cap_edges pairs; *n_inst / *n_edges get the full numbers.
+int dev_overlap_read(DeviceGraph *g, int32_t p, int32_t *inst_out, int64_t cap_inst, int64_t *n_inst,
+                     int32_t *edges_out, int64_t cap_edges, int64_t *n_edges);
 
 // Serving session: `slots` pattern slots on the graph's device with their own workspace.
 struct ServeSession;

@@ -37,12 +37,9 @@
 #include <mutex>
 #include <vector>
 
-#include "fx_dev.h"
-#include "search_util.h"
+#include "fx_kern.cuh"
 
 namespace fx {
-
-#define FULLMASK 0xFFFFFFFFu
 
 // window slot states.  A SEQ slot's root search ran out of its per-round budget: its remaining
 // search space is an ordered list of saved sub-searches (the first one's index in the slot's
@@ -53,14 +50,6 @@ enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3 };
 enum : int32_t { SS_PENDING = 0, SS_NONE = 1, SS_FOUND = 2 };
 constexpr int SPLIT_MAX = 15;  // pieces one split may create
 
-struct DevGraphView {
-    const VRec *vrec;
-    const uint32_t *runs;
-    const int32_t *adj;
-    const int32_t *lab_vtx;
-    int64_t nv;
-    int32_t words;  // used-bitmap words per pattern
-};
 
 // slot phases: free, greedy rounds, MNI pending, result ready
 enum : int32_t { PH_FREE = 0, PH_GREEDY = 1, PH_MNI = 2, PH_READY = 3 };
@@ -125,22 +114,6 @@ struct Batch {
     flexis_support_result *results;
 };
 
-// ------------------------------------------------------------------ warp depth-first search
-struct WarpState {
-    int32_t t[MAXN];                    // data vertex bound at each level
-    uint32_t lo[MAXN], hi[MAXN];        // driver slice of each level
-    uint32_t pos[MAXN], base[MAXN], mask[MAXN];
-    uint32_t conf[MAXN];                // backjump conflict set of each level (bits of levels)
-    uint32_t clo[MAXN][MAXN - 1], chi[MAXN][MAXN - 1];  // further slices (membership tests)
-    int32_t nchk[MAXN];
-    int32_t level;                      // level at suspension
-    int32_t floor;                      // lowest level this search may rebind (1: whole root)
-    // --- the fields above are the resumable search state (DFS_SAVE_WORDS words)
-    unsigned long long need[MAXN];      // neighbour labels each canonical vertex needs
-    LevelPlan L;
-    int32_t n;
-    int32_t pad[1];
-};
 constexpr int DFS_SAVE_WORDS = (int)(offsetof(WarpState, need) / 4);
 constexpr int DFS_SAVE_STRIDE = 192;  // words per saved sub-search
 constexpr int SUSP_STATUS = DFS_SAVE_WORDS;      // SS_* of the saved sub-search
@@ -150,265 +123,6 @@ static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large"
 constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
 constexpr uint32_t SEARCH_BUDGET = 4096;  // candidate chunks a root search runs per round
 
-__device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
-    return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
-}
-
-// Slice of v's neighbours carrying rank label `lab` (warp-cooperative: one load of up to 32
-// label runs, ballot on the label).  Returns an empty slice when the label is absent.
-__device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uint32_t lab,
-                                           uint32_t &lo, uint32_t &hi, unsigned long long &bytes) {
-    const int lane = threadIdx.x & 31;
-    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec + v));
-    bytes += 16;
-    const uint32_t adj = r.x, run = r.y, nrun = r.w >> 8;
-    lo = hi = 0;
-    for (uint32_t j0 = 0; j0 < nrun; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        const uint32_t e = (j <= nrun) ? __ldg(G.runs + run + j) : 0xFFFFFFFFu;
-        const uint32_t nx = __shfl_down_sync(FULLMASK, e, 1);
-        bytes += 4ull * min(32u, nrun + 1 - j0);
-        const bool hit = (j < nrun) && ((e >> 24) == lab);
-        const unsigned b = __ballot_sync(FULLMASK, hit);
-        if (b) {
-            const int s = __ffs(b) - 1;
-            const uint32_t es = __shfl_sync(FULLMASK, e, s);
-            uint32_t en = __shfl_sync(FULLMASK, nx, s);
-            if (s == 31) en = __ldg(G.runs + run + j0 + 32);
-            lo = adj + (es & 0xFFFFFFu);
-            hi = adj + (en & 0xFFFFFFu);
-            return;
-        }
-        const uint32_t last = __shfl_sync(FULLMASK, e, 31);
-        if ((last >> 24) > lab) return;  // runs are sorted by label
-    }
-}
-
-__device__ __forceinline__ bool contains(const int32_t *adj, uint32_t lo, uint32_t hi, int32_t c,
-                                         uint32_t &probes) {
-    uint32_t a = lo, b = hi;
-    while (a < b) {
-        const uint32_t m = (a + b) >> 1;
-        probes++;
-        if (__ldg(adj + m) < c) a = m + 1; else b = m;
-    }
-    if (a >= hi) return false;
-    probes++;
-    return __ldg(adj + a) == c;
-}
-
-// Prepare level i: slices of the bound neighbours at every backward level; the shortest one
-// drives the scan, the others are membership tests.  False if some slice is empty.
-__device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W, int i,
-                                            unsigned long long &bytes) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t lab = W.L.lab[i];
-    uint32_t bm = W.L.bmask[i];
-    uint32_t dlo = 0, dhi = 0, dlen = 0xFFFFFFFFu;
-    int nchk = 0;
-    while (bm) {
-        const int b = __ffs(bm) - 1;
-        bm &= bm - 1;
-        uint32_t lo, hi;
-        find_slice(G, W.t[b], lab, lo, hi, bytes);
-        if (lo == hi) return false;
-        const uint32_t len = hi - lo;
-        if (len < dlen) {
-            if (dlen != 0xFFFFFFFFu) {
-                if (lane == 0) { W.clo[i][nchk] = dlo; W.chi[i][nchk] = dhi; }
-                nchk++;
-            }
-            dlo = lo; dhi = hi; dlen = len;
-        } else {
-            if (lane == 0) { W.clo[i][nchk] = lo; W.chi[i][nchk] = hi; }
-            nchk++;
-        }
-    }
-    if (lane == 0) { W.lo[i] = dlo; W.hi[i] = dhi; W.nchk[i] = nchk; }
-    __syncwarp();
-    return true;
-}
-
-// Static one-hop filter: a data vertex can host a pattern vertex only if its degree is at least
-// the pattern vertex's and every label the pattern vertex's neighbours carry (ranks < 64) occurs
-// among its own neighbours.  Depends on the data vertex alone, so it rejects only vertices that
-// belong to no map at all.
-__device__ __forceinline__ bool vertex_fits(const DevGraphView &G, int32_t c, uint32_t deg_req,
-                                            unsigned long long need) {
-    const VRec *r = G.vrec + c;
-    const uint32_t deg = __ldg(&r->deg);
-    const unsigned long long have = __ldg(reinterpret_cast<const unsigned long long *>(&r->nbr_labels));
-    return deg >= deg_req && (have & need) == need;
-}
-
-// Candidate test at level i.  rej collects the earlier levels whose bound vertex caused a
-// rejection by injectivity (the conflict set of conflict-directed backjumping).
-template <int V>
-__device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
-                                                int32_t c, const uint32_t *used,
-                                                uint32_t &probes, uint32_t &rej) {
-    uint32_t im = W.L.injmask[i];
-    while (im) {
-        const int b = __ffs(im) - 1;
-        im &= im - 1;
-        if (W.t[b] == c) { rej |= 1u << b; return false; }
-    }
-    if constexpr (V == 1) {
-        // the used word and the vertex record do not depend on each other: load both before
-        // either decides, then test membership by interpolation search (same answers)
-        const uint32_t uw = used ? __ldcg(used + ((uint32_t)c >> 5)) : 0u;
-        const VRec *r = G.vrec + c;
-        const uint32_t deg = __ldg(&r->deg);
-        const unsigned long long have = __ldg(reinterpret_cast<const unsigned long long *>(&r->nbr_labels));
-        probes += used ? 5u : 4u;
-        if ((uw >> ((uint32_t)c & 31u)) & 1u) return false;
-        const unsigned long long need = W.need[W.L.vert[i]];
-        if (deg < W.L.deg[i] || (have & need) != need) return false;
-        const int nchk = W.nchk[i];
-        const int32_t *adj = G.adj;
-        auto at = [adj](uint32_t x) { return __ldg(adj + x); };
-        for (int k = 0; k < nchk; k++)
-            if (!interp_contains(at, W.clo[i][k], W.chi[i][k], c, probes)) return false;
-        return true;
-    }
-    if (used) {
-        probes++;
-        if (used_bit(used, c)) return false;
-    }
-    probes += 4;
-    if (!vertex_fits(G, c, W.L.deg[i], W.need[W.L.vert[i]])) return false;
-    const int nchk = W.nchk[i];
-    for (int k = 0; k < nchk; k++)
-        if (!contains(G.adj, W.clo[i][k], W.chi[i][k], c, probes)) return false;
-    return true;
-}
-
-// Lexicographically first map (in the level order of W.L) with level 0 bound to `root` and no
-// vertex in `used` (nullable).  On success W.t holds the map by level.
-//
-// Depth-first search with conflict-directed backjumping (Prosser, Computational Intelligence
-// 9(3), 1993): when every candidate of level i has failed, the search returns directly to the
-// deepest earlier level whose binding could change that outcome -- the levels that define
-// level i's candidate slices (its pattern neighbours), the levels whose vertex rejected a
-// candidate by injectivity, and the conflict levels handed up by deeper failures.  Levels in
-// between cannot make level i succeed, so skipping their remaining candidates removes only
-// subtrees without a map: the first map found in lexicographic order is unchanged.
-//
-// Resumable: with budget > 0 the search stops after `budget` candidate chunks and returns
-// DFS_SUSPENDED with its whole state in W (current level in W.level).  It may later continue
-// (resume = true) under a larger used set: bound vertices that have become used are dropped
-// (the search continues at the first such level with that level's remaining candidates) and
-// every popped candidate is re-tested against the used set.  Everything skipped before the
-// suspension failed under the smaller used set and fails under the larger one, so the first map
-// found is the first map avoiding the current used set.
-enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
-
-// V selects the membership test of check_candidate (0: binary search, 1: interpolation search).
-template <int V>
-__device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
-                       unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
-                       bool resume) {
-    const int lane = threadIdx.x & 31;
-    const int n = W.n;
-    int i = 1;
-    bool ok;
-    uint32_t hi = 0, pos = 0, base = 0, mask = 0, conf = 0;
-    if (!resume) {
-        if (lane == 0) { W.t[0] = root; W.floor = 1; }
-        __syncwarp();
-        if (used) {
-            bytes += 4;
-            if (used_bit(used, root)) return DFS_NONE;
-        }
-        bytes += 32;
-        if (!vertex_fits(G, root, W.L.deg[0], W.need[W.L.vert[0]])) return DFS_NONE;
-        ok = enter_level(G, W, 1, bytes);
-        if (ok) { hi = W.hi[1]; pos = W.lo[1]; }
-    } else {
-        if (used && used_bit(used, W.t[0])) return DFS_NONE;
-        i = W.level;
-        for (int l = 1; l < i; l++)
-            if (used && used_bit(used, W.t[l])) {
-                if (l < W.floor) return DFS_NONE;  // a binding this sub-search may not change
-                i = l;
-                break;
-            }
-        hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i]; conf = W.conf[i];
-        ok = true;
-    }
-    for (;;) {
-        if (!ok) {
-            // level i has no candidate left: jump to the deepest level of its conflict set;
-            // below the floor the search space of this (sub-)search is exhausted
-            const uint32_t cs = (conf | W.L.bmask[i]) & ((1u << i) - 1u);
-            const int h = 31 - __clz(cs);
-            if (h < W.floor) return DFS_NONE;
-            conf = W.conf[h] | (cs & ~(1u << h));
-            i = h;
-            hi = W.hi[i]; pos = W.pos[i]; base = W.base[i]; mask = W.mask[i];
-            ok = true;
-            continue;
-        }
-        if (mask == 0) {
-            if (pos >= hi) { ok = false; continue; }
-            if (budget && steps >= budget) {
-                if (lane == 0) {
-                    W.level = i;
-                    W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = 0; W.conf[i] = conf;
-                }
-                __syncwarp();
-                return DFS_SUSPENDED;
-            }
-            const uint32_t k = pos + lane;
-            bool good = false;
-            uint32_t rej = 0;
-            if (k < hi) good = check_candidate<V>(G, W, i, __ldg(G.adj + k), used, probes, rej);
-            mask = __ballot_sync(FULLMASK, good);
-            conf |= __reduce_or_sync(FULLMASK, rej);
-            bytes += 4ull * min(32u, hi - pos);
-            steps++;
-            base = pos;
-            pos += 32;
-            continue;
-        }
-        const int j = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int32_t c = __ldg(G.adj + base + j);
-        if (resume && used && used_bit(used, c)) continue;  // became used since the chunk scan
-        if (lane == 0) W.t[i] = c;
-        if (i == n - 1) {  // keep the position so that a later resume continues past this map
-            if (lane == 0) { W.level = i; W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
-            __syncwarp();
-            return DFS_FOUND;
-        }
-        if (lane == 0) { W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
-        __syncwarp();
-        ++i;
-        conf = 0;
-        ok = enter_level(G, W, i, bytes);
-        if (ok) { hi = W.hi[i]; pos = W.lo[i]; mask = 0; }
-    }
-}
-
-__device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
-                                          int32_t root, unsigned long long &bytes, uint32_t &probes,
-                                          uint32_t &steps) {
-    return dfs_run<0>(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
-}
-
-__device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {
-    const int lane = threadIdx.x & 31;
-    constexpr int WORDS = sizeof(LevelPlan) / 4;
-    if (lane < WORDS) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
-    if (lane < MAXN) W.need[lane] = P.need[lane];
-    if (lane == 0) W.n = P.n;
-    __syncwarp();
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
-    return v;
-}
 
 // ------------------------------------------------------------------ kernels
 constexpr int SEARCH_THREADS = 256;
@@ -432,7 +146,7 @@ __device__ void init_slot(const Batch &B, int p) {
     s.cursor = P.root_begin;
     s.W = B.Wmin;
     const bool nothing = P.status != FLEXIS_OK || (P.flags & FLEXIS_FLAG_ABSENT_LABEL) ||
-                         P.root_begin >= P.root_end;
+                         P.root_begin >= P.root_end || P.skip_mis;
     s.done = nothing ? 1 : 0;
     s.exhausted = nothing ? 1 : 0;
     s.phase = nothing ? PH_MNI : PH_GREEDY;
@@ -627,31 +341,6 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     if (lane == 0 && tot) atomicAdd(&B.ctl->bytes_greedy, tot);
 }
 
-// Block-wide exclusive scan of one int per thread; returns the total.
-__device__ __forceinline__ int block_scan(int v, int &excl, int *sh /* >= 33 ints */) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULLMASK, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < nw ? sh[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULLMASK, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < nw) sh[lane] = t;  // inclusive prefix of warp totals
-        if (lane == nw - 1) sh[32] = t;
-    }
-    __syncthreads();
-    excl = x - v + (w > 0 ? sh[w - 1] : 0);
-    const int total = sh[32];
-    __syncthreads();
-    return total;
-}
 
 // Map slots one commit examines: bounds the shared-memory inverted index (the window itself
 // can be larger; slots past the horizon are simply kept for the next round).
@@ -993,8 +682,10 @@ __global__ void k_mni_setup(Batch B) {
             const int p = sidx / MAXN, o = sidx % MAXN;
             const Plan &P = B.plans[p];
             const PatState &S = B.st[p];
+            // without a greedy phase nothing is known about the MNI: every orbit is searched
             const bool need = S.phase == PH_MNI && !S.cancelled && P.status == FLEXIS_OK && P.want_mni &&
-                              !(P.flags & FLEXIS_FLAG_ABSENT_LABEL) && S.count < P.cap && S.count > 0;
+                              !(P.flags & FLEXIS_FLAG_ABSENT_LABEL) &&
+                              (P.skip_mis || (S.count < P.cap && S.count > 0));
             if (need && o < P.n_orb) {
                 const int u = P.orb[o].vert[0];
                 len = P.lab_end[u] - P.lab_begin[u];
@@ -1113,6 +804,7 @@ __global__ void k_finalize(Batch B) {
     r.search_steps = (int64_t)S.steps;
     r.max_item_steps = (int32_t)S.max_steps;
     r.rounds = S.rounds;
+    r.mis_exact = -1;
     if (P.status == FLEXIS_OK) {
         const int64_t cap = P.cap;
         const int64_t mis = S.count < cap ? S.count : cap;
@@ -1121,6 +813,10 @@ __global__ void k_finalize(Batch B) {
             mni = -1;
         } else if (P.flags & FLEXIS_FLAG_ABSENT_LABEL) {
             mni = 0;
+        } else if (P.skip_mis) {
+            mni = cap;
+            for (int o = 0; o < P.n_orb; o++) mni = min(mni, min((int64_t)S.mni_cnt[o], cap));
+            if (P.root_begin >= P.root_end) mni = 0;  // no root: M is empty
         } else if (S.count >= cap || S.count == 0) {
             mni = S.count >= cap ? cap : 0;
             r.flags |= FLEXIS_FLAG_MNI_FROM_MIS;
@@ -1135,6 +831,14 @@ __global__ void k_finalize(Batch B) {
         r.mni = mni;
         const int64_t c = P.tau > 1 ? P.tau : 1;
         r.frequent = mis >= c ? 1 : 0;
+        if (P.mode == FLEXIS_MODE_EARLY) {
+            if (S.count >= cap && !P.skip_mis) r.flags |= FLEXIS_FLAG_MIS_SATURATED;
+            if (mni >= cap) r.flags |= FLEXIS_FLAG_MNI_SATURATED;
+        }
+        if (P.skip_mis) {
+            r.mis = -1;
+            r.frequent = 0;
+        }
         if (S.cancelled) {
             // stopped before its decision: mis counts the maps committed so far (a lower bound
             // of the pattern's mIS); nothing is decided
@@ -1147,54 +851,6 @@ __global__ void k_finalize(Batch B) {
 }
 
 // ------------------------------------------------------------------ device graph + workspaces
-#define CK(x)                                                                         \
-    do {                                                                              \
-        cudaError_t e_ = (x);                                                         \
-        if (e_ != cudaSuccess) {                                                      \
-            fprintf(stderr, "flexis: %s failed: %s\n", #x, cudaGetErrorString(e_));  \
-            return e_ == cudaErrorMemoryAllocation ? FLEXIS_E_NOMEM : FLEXIS_E_CUDA;  \
-        }                                                                             \
-    } while (0)
-
-// Evaluation workspace: P pattern slots with their used bitmaps, windows and work items.
-struct Workspace {
-    int32_t P = 0;           // pattern capacity
-    int64_t slots = 0;       // window-slot capacity (patterns x window size)
-    int64_t sel_slots = 0;   // selection-log capacity (patterns x maps)
-    int64_t bytes = 0;       // device bytes held
-    PatState *st = nullptr;
-    uint32_t *used = nullptr;
-    int32_t *dirty = nullptr;
-    int32_t clean = 0;  // patterns [0, clean) have all-zero used bitmaps between evaluations
-    int32_t *win_root = nullptr, *win_state = nullptr, *win_map = nullptr;
-    int2 *items = nullptr;
-    Ctl *ctl = nullptr;
-    int32_t *sel_buf = nullptr;
-    unsigned long long *mni_seg = nullptr;
-    uint32_t *susp = nullptr;
-    int32_t *alist = nullptr;
-    Plan *plans = nullptr;                   // device plan array (host-plan entry points)
-    flexis_support_result *results = nullptr;
-    int32_t plans_cap = 0;
-    Ctl *h_ctl = nullptr;                    // pinned
-};
-
-struct DeviceGraph {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    DevGraphView view{};
-    void *d_vrec = nullptr, *d_runs = nullptr, *d_adj = nullptr, *d_labvtx = nullptr;
-    int64_t bytes = 0;
-    int sm_count = 0, l2 = 0;
-    Workspace ws;
-    int32_t last_P = 0, last_sel = 0;
-    cudaEvent_t ev[2]{};
-    std::vector<cudaEvent_t> sev;
-    cudaGraphExec_t round_exec = nullptr;  // the captured round loop of the last level
-    std::vector<cudaEvent_t> gev;          // search-launch events inside the captured graph
-    int64_t graph_instantiations = 0, graph_fallbacks = 0;
-    int commit_small_blocks = 0;  // one wave of the small-horizon commit kernel
-};
 
 template <class T>
 static int upload(void **d, const std::vector<T> &h, cudaStream_t s, int64_t &bytes) {
@@ -1244,6 +900,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
     g->view.lab_vtx = (const int32_t *)g->d_labvtx;
     g->view.nv = hg.nv;
     g->view.words = (int32_t)std::max<int64_t>(1, (hg.nv + 31) / 32);
+    g->max_degree = hg.max_degree;
     if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
         cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)
@@ -1317,6 +974,7 @@ void dev_graph_destroy(DeviceGraph *g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     ws_free(g->ws);
+    enum_ws_destroy(g);
     cudaFree(g->d_vrec); cudaFree(g->d_runs); cudaFree(g->d_adj); cudaFree(g->d_labvtx);
     if (g->ev[0]) cudaEventDestroy(g->ev[0]);
     if (g->ev[1]) cudaEventDestroy(g->ev[1]);
@@ -1574,6 +1232,11 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     launches += 4;
     CK(cudaGetLastError());
     w.clean = std::max(clean0, P);
+    flexis_stats est{};
+    if (cfg.count_maps || cfg.exact_mis) {
+        const int rc2 = dev_enumerate(g, d_plans, P, d_results, stream, cfg, &est, t_start);
+        if (rc2) return rc2;
+    }
     CK(cudaEventRecord(g->ev[1], stream));
     CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
@@ -1588,6 +1251,10 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
         stats->search_launches = search_launches;
         stats->graph_launches = (int32_t)graph_launches;
         stats->d2h_bytes = (int64_t)sizeof(Ctl) * (rounds / R + 1);  // control-word reads
+        stats->kernel_launches += est.kernel_launches;
+        stats->enum_rows = est.enum_rows;
+        stats->enum_scanned = est.enum_scanned;
+        stats->enum_bytes = est.enum_bytes;
         float t = 0.f;
         cudaEventElapsedTime(&t, g->ev[0], g->ev[1]);
         stats->total_ms = t;

@@ -230,21 +230,32 @@ int64_t tau_exact(int64_t sigma, int64_t lam_num, int64_t lam_den, int n) {
     return (int64_t)(top / bot);
 }
 
+// The or-ed mode flags: the remaining base mode must be FLEXIS_MODE_EARLY or FLEXIS_MODE_FULL.
+static bool parse_mode(int mode, Plan &P) {
+    P.want_mni = (mode & FLEXIS_MODE_NO_MNI) ? 0 : 1;
+    P.count_maps = (mode & FLEXIS_MODE_COUNT_MAPS) ? 1 : 0;
+    P.skip_mis = (mode & FLEXIS_MODE_NO_MIS) ? 1 : 0;
+    P.exact_mis = (mode & FLEXIS_MODE_EXACT_MIS) ? 1 : 0;
+    mode &= ~(FLEXIS_MODE_NO_MNI | FLEXIS_MODE_COUNT_MAPS | FLEXIS_MODE_NO_MIS | FLEXIS_MODE_EXACT_MIS);
+    P.mode = mode;
+    if (!P.want_mni) P.flags |= FLEXIS_FLAG_MNI_SKIPPED;
+    if (P.skip_mis) P.flags |= FLEXIS_FLAG_MIS_SKIPPED;
+    return mode == FLEXIS_MODE_EARLY || mode == FLEXIS_MODE_FULL;
+}
+
 int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, int64_t lam_num,
                  int64_t lam_den, int mode, Plan &P) {
     memset(&P, 0, sizeof P);
     P.status = FLEXIS_E_INVALID;
     P.n = pat.n;
     P.sigma = sigma;
-    P.want_mni = (mode & FLEXIS_MODE_NO_MNI) ? 0 : 1;
-    mode &= ~FLEXIS_MODE_NO_MNI;
-    P.mode = mode;
-    if (!P.want_mni) P.flags |= FLEXIS_FLAG_MNI_SKIPPED;
+    const bool mode_ok = parse_mode(mode, P);
+    mode = P.mode;
     if (pat.n < 2 || pat.n > MAXN || pat.m < 0 || pat.labels == nullptr ||
         (pat.m > 0 && pat.edges == nullptr))
         return FLEXIS_E_INVALID;
     if (sigma < 1 || lam_den <= 0 || lam_num < 0 || lam_num > lam_den) return FLEXIS_E_INVALID;
-    if (mode != FLEXIS_MODE_EARLY && mode != FLEXIS_MODE_FULL) return FLEXIS_E_INVALID;
+    if (!mode_ok) return FLEXIS_E_INVALID;
     Pat p;
     p.n = pat.n;
     for (int i = 0; i < pat.n; i++) {
@@ -314,10 +325,11 @@ int compile_code(const HostGraph &g, const Code &code, int64_t sigma, int64_t la
     memset(&P, 0, sizeof P);
     P.n = code.n;
     P.sigma = sigma;
-    P.want_mni = (mode & FLEXIS_MODE_NO_MNI) ? 0 : 1;
-    mode &= ~FLEXIS_MODE_NO_MNI;
-    P.mode = mode;
-    if (!P.want_mni) P.flags |= FLEXIS_FLAG_MNI_SKIPPED;
+    if (!parse_mode(mode, P)) {
+        P.status = FLEXIS_E_INVALID;
+        return FLEXIS_E_INVALID;
+    }
+    mode = P.mode;
     P.n_edges = edge_count(pat_of_code(code));
     P.tau = tau_exact(sigma, lam_num, lam_den, code.n);
     const int64_t c = P.tau > 1 ? P.tau : 1;

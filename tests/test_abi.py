@@ -39,10 +39,29 @@ def test_every_declared_symbol_is_exported():
     assert set(names) == set(fx.SYMBOLS)
 
 
-def test_struct_sizes_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    # the C compiler's view of every public struct (size and field offsets) against the binding's
     import ctypes as C
-    assert C.sizeof(fx.flexis_options) == 64
-    assert C.sizeof(fx.flexis_support_result) == 80
+    import subprocess
+    structs = [fx.flexis_options, fx.flexis_pattern, fx.flexis_support_result, fx.flexis_plan,
+               fx.flexis_graph_info, fx.flexis_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "flexis.h"', 'int main(void) {']
+    for st in structs:
+        nm = st.__name__
+        lines.append(f'printf("{nm} %zu\\n", sizeof({nm}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{nm}.{f} %zu\\n", offsetof({nm}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st in structs:
+        nm = st.__name__
+        assert int(got[nm]) == C.sizeof(st), nm
+        for f, _ in st._fields_:
+            assert int(got[f"{nm}.{f}"]) == getattr(st, f).offset, (nm, f)
     assert C.sizeof(fx.flexis_plan) == 1024
 
 

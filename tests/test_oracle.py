@@ -526,3 +526,40 @@ def test_mining_matches_python_level_wise_miner():
         assert got == want, (sigma, lam, max_edges)
         saw_infrequent += sum(1 for c, f in wlev.values() if f < c)
     assert saw_infrequent >= 10
+
+
+# ----------------------------------------------------------------------------- overlap graph, MIS
+
+def test_maximum_independent_set_paper_examples():
+    # Sec. 2.4.2: the MIS of P1 in D has 2 maps; the Theorem 1 example (Fig. malVisual) has MIS 4
+    d = load("running_example.json")
+    g = graph_of(d)
+    assert g.max_independent_set(d["P1"]["labels"], d["P1"]["edges"]) == d["P1_MIS"] == 2
+    assert g.max_independent_set(d["P2"]["labels"], d["P2"]["edges"]) == d["P2_MIS"] == 1
+    inst, edges = g.overlap_graph(d["P1"]["labels"], d["P1"]["edges"])
+    # the six maps of P1 form three instances {d1,d2,d5}, {d2,d3,d6}, {d3,d4,d7} in a path
+    assert inst == [(0, 1, 4), (1, 2, 5), (2, 3, 6)] and edges == [(0, 1), (1, 2)]
+    m = load("malvisual.json")
+    gm = graph_of(m)
+    assert gm.max_independent_set(m["P"]["labels"], m["P"]["edges"]) == m["MIS"] == 4
+
+
+def test_overlap_graph_and_mis_match_brute_force():
+    for lab, src, dst, pl, pe, s in tiny_cases(120, 23):
+        edges = list(zip(src.tolist(), dst.tolist()))
+        M = bf.maps(lab.tolist(), edges, pl, pe)
+        g = oracle.Graph(lab, src, dst, seed=s)
+        sets = bf.vertex_sets(M)
+        got = g.overlap_graph(pl, pe)
+        assert got is not None
+        inst, cedges = got
+        assert inst == sorted(tuple(sorted(x)) for x in sets)
+        want_edges = [(a, b) for a in range(len(inst)) for b in range(a + 1, len(inst))
+                      if set(inst[a]) & set(inst[b])]
+        assert cedges == want_edges
+        if len(sets) <= 40:
+            big = g.max_independent_set(pl, pe, max_inst=40)
+            assert big == bf.maximum_is(M)
+            r = g.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=1)
+            # Theorem 1: mIS <= MIS <= n mIS
+            assert r["mis"] <= big <= len(pl) * r["mis"]
