@@ -125,10 +125,6 @@ typedef struct {
     int32_t root_order;      /* greedy root order (Sec. 3.2.2): 0 = by (H(seed, v), v), the seeded
                                 hash order (default); 1 = by vertex id, the order in which the
                                 paper's matcher visits the data vertices (seed unused) */
-    int32_t search_variant;  /* membership tests of the batched search: 0 = binary search (default);
-                                1 = interpolation search guarded by bisection, with the candidate's
-                                used-bit and vertex-record loads issued together.  Results are
-                                identical; 1 is checked on the host and not yet timed on a GPU */
     int32_t directed;        /* 0 = undirected data graph (each edge read both ways, the paper's
                                 loader, Sec. 4.1); 1 = directed: (src[e], dst[e]) is one arc and
                                 pattern edges are arcs too (the paper's directed matcher, Sec. 2.2) */
@@ -138,7 +134,7 @@ typedef struct {
     int64_t exact_mis_nodes; /* FLEXIS_MODE_EXACT_MIS: branch-and-bound nodes per pattern (0 = 2^24) */
     int32_t exact_mis_maps;  /* FLEXIS_MODE_EXACT_MIS: largest number of distinct instances whose
                                 overlap graph is searched (0 = 2048, at most 4096) */
-    int32_t reserved[5];
+    int32_t reserved[6];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected

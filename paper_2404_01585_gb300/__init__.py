@@ -56,9 +56,9 @@ class flexis_options(C.Structure):
                 ("record_selected", C.c_int32), ("search_budget", C.c_int32),
                 ("split_pieces", C.c_int32), ("sub_searches", C.c_int32), ("timing", C.c_int32),
                 ("graphs", C.c_int32), ("deadline_ms", C.c_int32), ("root_order", C.c_int32),
-                ("search_variant", C.c_int32), ("directed", C.c_int32), ("maps_cap", C.c_int64),
+                ("directed", C.c_int32), ("maps_cap", C.c_int64),
                 ("frontier_rows", C.c_int64), ("exact_mis_nodes", C.c_int64),
-                ("exact_mis_maps", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("exact_mis_maps", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class flexis_pattern(C.Structure):
@@ -223,7 +223,7 @@ class Graph:
 
     Keyword options are the fields of flexis_options: seed, device, window_min, window_max,
     search_blocks, record_selected, search_budget, split_pieces, sub_searches, timing, graphs,
-    deadline_ms, root_order, search_variant, directed, maps_cap, frontier_rows, exact_mis_nodes,
+    deadline_ms, root_order, directed, maps_cap, frontier_rows, exact_mis_nodes,
     exact_mis_maps (meanings in include/flexis.h).  They apply to every
     call on the graph and to servers started on it."""
 

@@ -103,7 +103,6 @@ EvalConfig config_for(const flexis_graph *g, int32_t P) {
     c.timing = g->opt.timing != 0;
     c.graphs = g->opt.graphs >= 0;
     c.deadline_ms = g->opt.deadline_ms;
-    c.search_variant = g->opt.search_variant == 1 ? 1 : 0;
     c.search_budget = g->opt.search_budget != 0 ? g->opt.search_budget : P < SMALL_BATCH ? SMALL_BATCH_BUDGET : 0;
     c.split_pieces = g->opt.split_pieces;
     c.sub_searches = g->opt.sub_searches;

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_extend(EnumPass E) {
                 uint32_t rej = 0;
                 if (k < hi) {
                     c = __ldg(E.G.adj + k);
-                    good = check_candidate<0>(E.G, W, j, c, nullptr, probes, rej);
+                    good = check_candidate(E.G, W, j, c, nullptr, probes, rej);
                 }
                 const unsigned mask = __ballot_sync(FULLMASK, good);
                 scanned += min(32u, hi - pos);

@@ -20,7 +20,6 @@ struct EvalConfig {
     bool timing = false;        // per-launch CUDA events around the search kernel
     bool graphs = true;         // replay the round loop as a captured CUDA graph
     int32_t deadline_ms = 0;    // > 0: patterns undecided after this long stop with FLEXIS_E_TIMEOUT
-    int32_t search_variant = 0; // 1: interpolation-search membership tests (see search_util.h)
     bool count_maps = false;    // some plan wants n_maps (or may: plans already on the device)
     bool exact_mis = false;     // some plan wants the exact MIS
     int64_t maps_cap = 0;       // n_maps saturation (0: default)

@@ -10,7 +10,6 @@
 #include <vector>
 
 #include "fx_dev.h"
-#include "search_util.h"
 
 namespace fx {
 
@@ -135,7 +134,6 @@ __device__ __forceinline__ bool vertex_fits(const DevGraphView &G, int32_t c, ui
 
 // Candidate test at level i.  rej collects the earlier levels whose bound vertex caused a
 // rejection by injectivity (the conflict set of conflict-directed backjumping).
-template <int V>
 __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const WarpState &W, int i,
                                                 int32_t c, const uint32_t *used,
                                                 uint32_t &probes, uint32_t &rej) {
@@ -144,24 +142,6 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
         const int b = __ffs(im) - 1;
         im &= im - 1;
         if (W.t[b] == c) { rej |= 1u << b; return false; }
-    }
-    if constexpr (V == 1) {
-        // the used word and the vertex record do not depend on each other: load both before
-        // either decides, then test membership by interpolation search (same answers)
-        const uint32_t uw = used ? __ldcg(used + ((uint32_t)c >> 5)) : 0u;
-        const VRec *r = G.vrec + c;
-        const uint32_t deg = __ldg(&r->deg);
-        const unsigned long long have = __ldg(reinterpret_cast<const unsigned long long *>(&r->nbr_labels));
-        probes += used ? 5u : 4u;
-        if ((uw >> ((uint32_t)c & 31u)) & 1u) return false;
-        const unsigned long long need = W.need[W.L.vert[i]];
-        if (deg < W.L.deg[i] || (have & need) != need) return false;
-        const int nchk = W.nchk[i];
-        const int32_t *adj = G.adj;
-        auto at = [adj](uint32_t x) { return __ldg(adj + x); };
-        for (int k = 0; k < nchk; k++)
-            if (!interp_contains(at, W.clo[i][k], W.chi[i][k], c, probes)) return false;
-        return true;
     }
     if (used) {
         probes++;
@@ -195,9 +175,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // found is the first map avoiding the current used set.
 enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
 
-// V selects the membership test of check_candidate (0: binary search, 1: interpolation search).
-template <int V>
-__device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
+__device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                        unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
                        bool resume) {
     const int lane = threadIdx.x & 31;
@@ -254,7 +232,7 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
             const uint32_t k = pos + lane;
             bool good = false;
             uint32_t rej = 0;
-            if (k < hi) good = check_candidate<V>(G, W, i, __ldg(G.adj + k), used, probes, rej);
+            if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes, rej);
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
             bytes += 4ull * min(32u, hi - pos);
@@ -285,7 +263,7 @@ __device__ int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used
 __device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
                                           int32_t root, unsigned long long &bytes, uint32_t &probes,
                                           uint32_t &steps) {
-    return dfs_run<0>(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
+    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
 }
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {

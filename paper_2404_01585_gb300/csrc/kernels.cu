@@ -204,7 +204,6 @@ __device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, in
 // A search that uses up its per-round budget is saved; if it heads its slot it is also split:
 // the unscanned candidates of its shallowest level with any left go to up to five new
 // sub-searches, in order, and a continuation takes over everything after them.
-template <int V>
 __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     __shared__ WarpState ws[SEARCH_THREADS / 32];
     const int lane = threadIdx.x & 31;
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r = dfs_run<V>(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
+        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
         int sidA = sid_in;
         if (r == DFS_SUSPENDED) {
             const bool head = !resume || seq[0] == sid_in;
@@ -1024,7 +1023,7 @@ static Batch make_batch(const DeviceGraph *g, const Workspace &w, const Plan *pl
 
 static int search_grid(const DeviceGraph *g, const EvalConfig &cfg) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<0>, SEARCH_THREADS, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, SEARCH_THREADS, 0) != cudaSuccess)
         per_sm = 1;
     return cfg.search_blocks > 0 ? cfg.search_blocks : g->sm_count * std::max(1, per_sm);
 }
@@ -1040,15 +1039,12 @@ static void launch_commit(const Batch &B, int q, bool small, int commit_blocks, 
         k_commit<KMAP><<<commit_blocks, COMMIT_THREADS, smem, stream>>>(B, q);
 }
 
-static void launch_search(const Batch &B, int q, int variant, int sblocks, cudaStream_t stream) {
-    if (variant == 1)
-        k_search<1><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
-    else
-        k_search<0><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+static void launch_search(const Batch &B, int q, int sblocks, cudaStream_t stream) {
+    k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
 }
 
 static int capture_rounds(DeviceGraph *g, const Batch &B, int R, bool small, int commit_blocks, size_t smem,
-                          int variant, int sblocks, cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl,
+                          int sblocks, cudaStream_t stream, Ctl *h_ctl, Ctl *d_ctl,
                           const cudaEvent_t *tev) {
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1060,7 +1056,7 @@ static int capture_rounds(DeviceGraph *g, const Batch &B, int R, bool small, int
         // an event record node needs the external flag (a plain record inside a capture only
         // orders streams)
         if (tev) cudaEventRecordWithFlags(tev[2 * r], stream, cudaEventRecordExternal);
-        launch_search(B, r & 1, variant, sblocks, stream);
+        launch_search(B, r & 1, sblocks, stream);
         if (tev) cudaEventRecordWithFlags(tev[2 * r + 1], stream, cudaEventRecordExternal);
     }
     cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
@@ -1162,7 +1158,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
             CK(cudaEventCreate(&e));
             g->gev.push_back(e);
         }
-        if (!capture_rounds(g, B, R, small_commit, commit_blocks, smem, cfg.search_variant, sblocks, stream,
+        if (!capture_rounds(g, B, R, small_commit, commit_blocks, smem, sblocks, stream,
                             w.h_ctl, w.ctl,
                             cfg.timing ? g->gev.data() : nullptr)) {
             for (;;) {
@@ -1199,7 +1195,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
                 }
                 CK(cudaEventRecord(g->sev[evi], stream));
             }
-            launch_search(B, q, cfg.search_variant, sblocks, stream);
+            launch_search(B, q, sblocks, stream);
             if (cfg.timing) {
                 CK(cudaEventRecord(g->sev[evi + 1], stream));
                 evi += 2;
@@ -1406,7 +1402,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
         for (int r = 0; r < 2; r++, round++) {
             const int q = (int)(round & 1);
             k_commit<KMAP><<<1, COMMIT_THREADS, commit_smem(0), stream>>>(B, q);
-            k_search<0><<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
+            k_search<<<sblocks, SEARCH_THREADS, 0, stream>>>(B, q);
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&h_ctl, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
@@ -1562,7 +1558,7 @@ int serve_step(ServeSession *s, const int32_t *admit_slots, const Plan *admit_pl
     }
     const int q = (int)(s->round & 1);
     k_commit<KMAP><<<s->slots, COMMIT_THREADS, commit_smem(s->Wmax), s->stream>>>(B, q);
-    k_search<0><<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
+    k_search<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B, q);
     s->round++;
     k_mni_setup<<<1, 1024, 0, s->stream>>>(B);
     k_mni<<<s->sblocks, SEARCH_THREADS, 0, s->stream>>>(B);

@@ -1,9 +1,6 @@
 """Host logic of the library checked as plain C++ (no GPU): each check program is compiled
 with the host sources it tests and compared there with a plain recomputation.
 
-* host_search_check.cpp -- the membership search shared with the search kernels
-  (csrc/search_util.h) against std::binary_search on sorted runs of many shapes, with the
-  bisection bound on the loads it makes.
 * host_graph_check.cpp -- the data-graph build (csrc/graph.cpp): label ranks, deduplicated and
   sorted adjacency, label runs, vertex records, the root index in both root orders, label pairs,
   dropped self-loops and repeats, on 144 random graphs.
@@ -35,10 +32,6 @@ def run_check(main_cpp, *sources):
         r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails 0" in r.stdout, r.stdout
-
-
-def test_interpolation_search_matches_binary_search():
-    run_check("host_search_check.cpp")
 
 
 def test_host_graph_build_matches_plain_recomputation():
