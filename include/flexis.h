@@ -139,12 +139,17 @@ typedef struct {
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
  * edges edges[2*m] as 0-based vertex pairs.  Repeated edges are allowed and merged; self-loops
- * and disconnected patterns are FLEXIS_E_INVALID.  2 <= n <= 8.                                */
+ * and disconnected patterns are FLEXIS_E_INVALID.  2 <= n <= 8.
+ * edge_labels[m]: labels of the edges, for graphs loaded with flexis_load_graph_edge_labels
+ * (required there, and NULL otherwise).  Such a pattern is evaluated in its extended form (each
+ * edge subdivided by a vertex carrying the edge's label, Sec. 2.3.5), which must have at most
+ * 8 vertices (n + m <= 8) and no repeated edge.                                              */
 typedef struct {
     int32_t n;
     int32_t m;
     const int32_t *labels;
     const int32_t *edges;
+    const int32_t *edge_labels;
 } flexis_pattern;
 
 /* Support of one pattern (all integer). */
@@ -186,6 +191,10 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the graph */
     int32_t sm_count;
     int32_t l2_bytes;
+    int64_t n_input_vertices; /* vertices the caller passed (before the edge-label extension) */
+    int32_t edge_label_base;  /* label id of edge label 0 in the extended graph; -1 without
+                                 edge labels */
+    int32_t directed;         /* 1 for a directed graph (options.directed) */
 } flexis_graph_info;
 
 /* Counters of the last support / batch / mining call on a graph (diagnostics, timing). */
@@ -238,6 +247,20 @@ void flexis_default_options(flexis_options *opt);
 int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
                       const int32_t *src, const int32_t *dst, const flexis_options *opt,
                       flexis_graph **out);
+
+/* Load an edge-labelled data graph (Sec. 2.3.5, extended core graphs): every kept edge (u, v)
+ * with label edge_labels[e] >= 0 is replaced by two edges (u, w), (w, v) through a new vertex w
+ * whose label is edge_label_base + edge_labels[e], edge_label_base = 1 + the largest vertex
+ * label.  The resident graph is that vertex-labelled extended graph (n_vertices + kept edges
+ * vertices; flexis_graph_info reports both counts and the base), and every evaluation, mining
+ * run and served request works on it: a pattern passes its edge labels in
+ * flexis_pattern.edge_labels and is extended the same way, so tau, mis and mni are those of the
+ * extended pattern (n + m vertices).  Mined patterns are vertex-labelled patterns of the extended
+ * graph.  Self-loops are dropped; of repeated edges between the same two vertices (in either
+ * direction) the first one, with its label, is kept.                                          */
+int flexis_load_graph_edge_labels(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
+                                  const int32_t *src, const int32_t *dst, const int32_t *edge_labels,
+                                  const flexis_options *opt, flexis_graph **out);
 void flexis_free_graph(flexis_graph *g);
 int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out);
 

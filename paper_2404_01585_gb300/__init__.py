@@ -63,7 +63,7 @@ class flexis_options(C.Structure):
 
 class flexis_pattern(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("labels", C.POINTER(C.c_int32)),
-                ("edges", C.POINTER(C.c_int32))]
+                ("edges", C.POINTER(C.c_int32)), ("edge_labels", C.POINTER(C.c_int32))]
 
 
 class flexis_support_result(C.Structure):
@@ -94,7 +94,8 @@ class flexis_plan(C.Structure):
 class flexis_graph_info(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("n_arcs", C.c_int64), ("n_self_loops", C.c_int64),
                 ("n_duplicates", C.c_int64), ("n_labels", C.c_int32), ("max_degree", C.c_int32),
-                ("device_bytes", C.c_int64), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32)]
+                ("device_bytes", C.c_int64), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32),
+                ("n_input_vertices", C.c_int64), ("edge_label_base", C.c_int32), ("directed", C.c_int32)]
 
 
 class flexis_stats(C.Structure):
@@ -120,6 +121,8 @@ SYMBOLS = {
     "flexis_lambda_quantize": (C.c_int, [C.c_double, _I64P]),
     "flexis_load_graph": (C.c_int, [C.c_int64, _I32P, C.c_int64, _I32P, _I32P,
                                      C.POINTER(flexis_options), C.POINTER(_P)]),
+    "flexis_load_graph_edge_labels": (C.c_int, [C.c_int64, _I32P, C.c_int64, _I32P, _I32P, _I32P,
+                                                 C.POINTER(flexis_options), C.POINTER(_P)]),
     "flexis_free_graph": (None, [_P]),
     "flexis_graph_info_get": (C.c_int, [_P, C.POINTER(flexis_graph_info)]),
     "flexis_support": (C.c_int, [_P, C.POINTER(flexis_pattern), C.c_int64, C.c_double, C.c_int32,
@@ -201,13 +204,16 @@ def _i32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
 
 
-def make_pattern(labels, edges):
-    """(flexis_pattern, keepalive) from label list and edge list."""
+def make_pattern(labels, edges, edge_labels=None):
+    """(flexis_pattern, keepalive) from label list, edge list and (edge-labelled graphs) the
+    edges' labels."""
     lab = _i32(labels)
     e = _i32(np.asarray(edges, dtype=np.int32).reshape(-1)) if len(edges) else np.zeros(2, np.int32)
     m = (e.size // 2) if len(edges) else 0
-    p = flexis_pattern(lab.size, m, lab.ctypes.data_as(_I32P), e.ctypes.data_as(_I32P))
-    return p, (lab, e)
+    el = None if edge_labels is None else _i32(edge_labels)
+    p = flexis_pattern(lab.size, m, lab.ctypes.data_as(_I32P), e.ctypes.data_as(_I32P),
+                       el.ctypes.data_as(_I32P) if el is not None else None)
+    return p, (lab, e, el)
 
 
 def default_options(**kw) -> flexis_options:
@@ -227,7 +233,7 @@ class Graph:
     exact_mis_maps (meanings in include/flexis.h).  They apply to every
     call on the graph and to servers started on it."""
 
-    def __init__(self, labels, src, dst, **options):
+    def __init__(self, labels, src, dst, edge_labels=None, **options):
         L = lib()
         self._labels = _i32(labels)
         self._src = _i32(src)
@@ -237,10 +243,18 @@ class Graph:
         ne = self._src.size
         srcp = self._src if ne else np.zeros(1, np.int32)
         dstp = self._dst if ne else np.zeros(1, np.int32)
-        rc = L.flexis_load_graph(self._labels.size, self._labels.ctypes.data_as(_I32P), ne,
-                                 srcp.ctypes.data_as(_I32P), dstp.ctypes.data_as(_I32P),
-                                 C.byref(self.options), C.byref(h))
-        _check(rc, "flexis_load_graph")
+        if edge_labels is None:
+            rc = L.flexis_load_graph(self._labels.size, self._labels.ctypes.data_as(_I32P), ne,
+                                     srcp.ctypes.data_as(_I32P), dstp.ctypes.data_as(_I32P),
+                                     C.byref(self.options), C.byref(h))
+            _check(rc, "flexis_load_graph")
+        else:
+            el = _i32(edge_labels)
+            elp = el if ne else np.zeros(1, np.int32)
+            rc = L.flexis_load_graph_edge_labels(self._labels.size, self._labels.ctypes.data_as(_I32P), ne,
+                                                 srcp.ctypes.data_as(_I32P), dstp.ctypes.data_as(_I32P),
+                                                 elp.ctypes.data_as(_I32P), C.byref(self.options), C.byref(h))
+            _check(rc, "flexis_load_graph_edge_labels")
         self._h = h
         del self._src, self._dst
 
@@ -265,8 +279,8 @@ class Graph:
         return {k: getattr(i, k) for k, _ in i._fields_}
 
     def support(self, labels, edges, sigma, lam=None, *, lam_num=None, lam_den=LAMBDA_DEN,
-                mode=FLEXIS_MODE_EARLY) -> dict:
-        p, keep = make_pattern(labels, edges)
+                mode=FLEXIS_MODE_EARLY, edge_labels=None) -> dict:
+        p, keep = make_pattern(labels, edges, edge_labels)
         r = flexis_support_result()
         if lam_num is not None:
             rc = lib().flexis_support_q(self._h, C.byref(p), sigma, lam_num, lam_den, mode, C.byref(r))
@@ -278,8 +292,8 @@ class Graph:
     def _patterns(self, patterns):
         arr = (flexis_pattern * max(1, len(patterns)))()
         keep = []
-        for i, (l, e) in enumerate(patterns):
-            p, k = make_pattern(l, e)
+        for i, pt in enumerate(patterns):  # (labels, edges) or (labels, edges, edge_labels)
+            p, k = make_pattern(*pt)
             arr[i] = p
             keep.append(k)
         return arr, keep
@@ -341,10 +355,10 @@ class Graph:
                "flexis_selected_maps")
         return [tuple(int(x) for x in buf[j, :n]) for j in range(k.value)]
 
-    def overlap_graph(self, labels, edges, cap_instances=1 << 12, cap_edges=1 << 22):
+    def overlap_graph(self, labels, edges, cap_instances=1 << 12, cap_edges=1 << 22, edge_labels=None):
         """flexis_overlap_graph: (instances, conflict edges), instances as sorted vertex tuples
         in ascending order, edges as (a, b) pairs, a < b, ascending."""
-        p, keep = make_pattern(labels, edges)
+        p, keep = make_pattern(labels, edges, edge_labels)
         inst = np.zeros((max(cap_instances, 1), 8), np.int32)
         ed = np.zeros((max(cap_edges, 1), 2), np.int32)
         ni, ne = C.c_int64(), C.c_int64()
@@ -423,19 +437,23 @@ def canonical_code(labels, edges):
 def generate_candidates(patterns, max_edges=0):
     arr = (flexis_pattern * max(1, len(patterns)))()
     keep = []
-    for i, (l, e) in enumerate(patterns):
-        p, k = make_pattern(l, e)
+    for i, pt in enumerate(patterns):
+        p, k = make_pattern(*pt)
         arr[i] = p
         keep.append(k)
     cap = 1 << 18
-    on = np.zeros(cap, np.int32)
-    ol = np.zeros(cap * 8, np.int32)
-    ob = np.zeros(cap, np.uint32)
-    k = lib().flexis_generate_candidates(arr, len(patterns), max_edges, on.ctypes.data_as(_I32P),
-                                         ol.ctypes.data_as(_I32P),
-                                         ob.ctypes.data_as(C.POINTER(C.c_uint32)), cap)
-    if k < 0:
-        raise FlexisError(FLEXIS_E_INVALID if k == -1 else FLEXIS_E_NOMEM, "flexis_generate_candidates")
+    while True:
+        on = np.zeros(cap, np.int32)
+        ol = np.zeros(cap * 8, np.int32)
+        ob = np.zeros(cap, np.uint32)
+        k = lib().flexis_generate_candidates(arr, len(patterns), max_edges, on.ctypes.data_as(_I32P),
+                                             ol.ctypes.data_as(_I32P),
+                                             ob.ctypes.data_as(C.POINTER(C.c_uint32)), cap)
+        if k == FLEXIS_E_INVALID:
+            raise FlexisError(FLEXIS_E_INVALID, "flexis_generate_candidates")
+        if k >= 0:
+            break
+        cap = -k  # the output needs -k entries
     return [(int(on[i]), tuple(int(x) for x in ol[8 * i: 8 * i + on[i]]), int(ob[i])) for i in range(k)]
 
 
@@ -448,8 +466,8 @@ class Server:
         self._h = h
         self.graph = graph
 
-    def submit(self, request_id, labels, edges, sigma, lam, mode=FLEXIS_MODE_EARLY):
-        p, keep = make_pattern(labels, edges)
+    def submit(self, request_id, labels, edges, sigma, lam, mode=FLEXIS_MODE_EARLY, edge_labels=None):
+        p, keep = make_pattern(labels, edges, edge_labels)
         return lib().flexis_serve_submit(self._h, request_id, C.byref(p), sigma, float(lam), mode)
 
     def poll(self, max_results=4096):

@@ -17,6 +17,9 @@ struct flexis_graph {
     DeviceGraph *dg = nullptr;
     flexis_options opt{};
     flexis_stats last{};
+    int64_t n_input_vertices = 0;  // vertices the caller passed
+    int32_t edge_label_base = -1;  // label of edge label 0 in the extended graph; -1: none
+    int64_t input_self_loops = 0, input_duplicates = 0;  // of the caller's edge list
 };
 
 struct flexis_pattern_set {
@@ -156,6 +159,57 @@ int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result 
     return FLEXIS_OK;
 }
 
+// A caller's pattern in the form the graph holds: on an edge-labelled graph, each pattern edge
+// (a, b) with label l becomes a vertex of label edge_label_base + l joined to a and b (the
+// extended pattern of Sec. 2.3.5).  `buf` keeps the extended arrays alive.
+struct PatBuf {
+    std::vector<int32_t> labels, edges;
+};
+
+int user_pattern(const flexis_graph *g, const flexis_pattern &in, PatBuf &buf, flexis_pattern &out) {
+    out = in;
+    if (g->edge_label_base < 0) {
+        if (in.edge_labels) return FLEXIS_E_INVALID;  // edge labels on a graph without them
+        return FLEXIS_OK;
+    }
+    if (!in.edge_labels || in.n < 1 || in.m < 1 || !in.labels || !in.edges || in.n + in.m > MAXN)
+        return FLEXIS_E_INVALID;
+    buf.labels.assign(in.labels, in.labels + in.n);
+    buf.edges.clear();
+    std::vector<std::pair<int32_t, int32_t>> seen;
+    for (int e = 0; e < in.m; e++) {
+        int32_t a = in.edges[2 * e], b = in.edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= in.n || b >= in.n || a == b || in.edge_labels[e] < 0) return FLEXIS_E_INVALID;
+        const auto key = std::make_pair(std::min(a, b), std::max(a, b));
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) return FLEXIS_E_INVALID;
+        seen.push_back(key);
+        const int32_t w = in.n + e;
+        buf.labels.push_back(g->edge_label_base + in.edge_labels[e]);
+        buf.edges.insert(buf.edges.end(), {a, w, w, b});
+    }
+    out.n = in.n + in.m;
+    out.m = 2 * in.m;
+    out.labels = buf.labels.data();
+    out.edges = buf.edges.data();
+    out.edge_labels = nullptr;
+    return FLEXIS_OK;
+}
+
+// compile_plan on the graph's form of a caller's pattern (an invalid one gives an error plan)
+int compile_user(const flexis_graph *g, const flexis_pattern &pat, int64_t sigma, int64_t num, int64_t den,
+                 int mode, Plan &P) {
+    PatBuf buf;
+    flexis_pattern q;
+    const int rc = user_pattern(g, pat, buf, q);
+    if (rc) {
+        memset(&P, 0, sizeof P);
+        P.status = rc;
+        P.n = pat.n;
+        return rc;
+    }
+    return compile_plan(g->hg, q, sigma, num, den, mode, P);
+}
+
 void pattern_of_code(const flexis_graph *g, const Code &c, std::vector<int32_t> &labels,
                      std::vector<int32_t> &edges) {
     Pat p = pat_of_code(c);
@@ -214,7 +268,62 @@ int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges
     if (rc) return rc;
     rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
     if (rc) return rc;
+    g->n_input_vertices = n_vertices;
+    g->input_self_loops = g->hg.self_loops;
+    g->input_duplicates = g->hg.duplicates;
     *out = g.release();
+    return FLEXIS_OK;
+}
+
+int flexis_load_graph_edge_labels(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
+                                  const int32_t *src, const int32_t *dst, const int32_t *edge_labels,
+                                  const flexis_options *opt, flexis_graph **out) {
+    if (!out || n_vertices < 0 || n_edges < 0 || (n_vertices > 0 && !labels) ||
+        (n_edges > 0 && (!src || !dst || !edge_labels)))
+        return FLEXIS_E_INVALID;
+    int32_t base = 0;
+    for (int64_t v = 0; v < n_vertices; v++) {
+        if (labels[v] < 0) return FLEXIS_E_INVALID;
+        base = std::max(base, labels[v] + 1);
+    }
+    // kept edges: no self-loop, first occurrence of each vertex pair (either direction)
+    std::vector<std::pair<uint64_t, int64_t>> key((size_t)n_edges);
+    int64_t loops = 0;
+    for (int64_t e = 0; e < n_edges; e++) {
+        if (src[e] < 0 || dst[e] < 0 || src[e] >= n_vertices || dst[e] >= n_vertices || edge_labels[e] < 0)
+            return FLEXIS_E_INVALID;
+        const uint64_t a = (uint64_t)std::min(src[e], dst[e]), b = (uint64_t)std::max(src[e], dst[e]);
+        key[(size_t)e] = {a << 32 | b, e};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int64_t> kept;
+    for (size_t i = 0; i < key.size(); i++) {
+        const int64_t e = key[i].second;
+        if (src[e] == dst[e]) { loops++; continue; }
+        if (i > 0 && key[i - 1].first == key[i].first) continue;
+        kept.push_back(e);
+    }
+    std::sort(kept.begin(), kept.end());
+    const int64_t dups = n_edges - loops - (int64_t)kept.size();
+    const int64_t nk = (int64_t)kept.size();
+    if (n_vertices + nk >= (int64_t)INT32_MAX) return FLEXIS_E_UNSUPPORTED;
+    std::vector<int32_t> lab2((size_t)(n_vertices + nk)), s2((size_t)(2 * nk)), d2((size_t)(2 * nk));
+    std::copy(labels, labels + n_vertices, lab2.begin());
+    for (int64_t k = 0; k < nk; k++) {
+        const int64_t e = kept[(size_t)k];
+        const int32_t w = (int32_t)(n_vertices + k);
+        lab2[(size_t)(n_vertices + k)] = base + edge_labels[e];
+        s2[(size_t)(2 * k)] = src[e];
+        d2[(size_t)(2 * k)] = w;
+        s2[(size_t)(2 * k + 1)] = w;
+        d2[(size_t)(2 * k + 1)] = dst[e];
+    }
+    int rc = flexis_load_graph(n_vertices + nk, lab2.data(), 2 * nk, s2.data(), d2.data(), opt, out);
+    if (rc) return rc;
+    (*out)->n_input_vertices = n_vertices;
+    (*out)->edge_label_base = base;
+    (*out)->input_self_loops = loops;
+    (*out)->input_duplicates = dups;
     return FLEXIS_OK;
 }
 
@@ -229,8 +338,11 @@ int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out) {
     memset(out, 0, sizeof *out);
     out->n_vertices = g->hg.nv;
     out->n_arcs = g->hg.n_arcs;
-    out->n_self_loops = g->hg.self_loops;
-    out->n_duplicates = g->hg.duplicates;
+    out->n_self_loops = g->input_self_loops;
+    out->n_duplicates = g->input_duplicates;
+    out->n_input_vertices = g->n_input_vertices;
+    out->edge_label_base = g->edge_label_base;
+    out->directed = g->opt.directed ? 1 : 0;
     out->n_labels = g->hg.nl;
     out->max_degree = g->hg.max_degree;
     out->device_bytes = dev_graph_bytes(g->dg);
@@ -246,7 +358,7 @@ int flexis_support_q(flexis_graph *g, const flexis_pattern *pattern, int64_t sig
                      flexis_support_result *out) {
     if (!g || !pattern || !out) return FLEXIS_E_INVALID;
     std::vector<Plan> plans(1);
-    int rc = compile_plan(g->hg, *pattern, sigma, lambda_num, lambda_den, mode, plans[0]);
+    int rc = compile_user(g, *pattern, sigma, lambda_num, lambda_den, mode, plans[0]);
     if (rc) return rc;
     flexis_support_result r;
     rc = eval_plans(g, plans, &r);
@@ -269,7 +381,7 @@ int flexis_compile(flexis_graph *g, const flexis_pattern *patterns, const int64_
         return FLEXIS_E_INVALID;
     for (int32_t i = 0; i < count; i++) {
         Plan P;
-        compile_plan(g->hg, patterns[i], sigma[i], lambda_num[i], lambda_den, mode, P);
+        compile_user(g, patterns[i], sigma[i], lambda_num[i], lambda_den, mode, P);
         memset(&plans_out[i], 0, sizeof(flexis_plan));
         memcpy(&plans_out[i], &P, sizeof P);
     }
@@ -295,7 +407,7 @@ int flexis_support_batch(flexis_graph *g, const flexis_pattern *patterns, const 
                 plans[(size_t)i].n = patterns[i].n;
                 continue;
             }
-            compile_plan(g->hg, patterns[i], sigma[i], num, LAMBDA_DEN, mode, plans[(size_t)i]);
+            compile_user(g, patterns[i], sigma[i], num, LAMBDA_DEN, mode, plans[(size_t)i]);
         }
     };
     for (int t = 1; t < T; t++) th.emplace_back(work, t);
@@ -342,7 +454,7 @@ int flexis_overlap_graph(flexis_graph *g, const flexis_pattern *pattern, int32_t
         (cap_instances > 0 && !instances_out) || (cap_edges > 0 && !edges_out))
         return FLEXIS_E_INVALID;
     std::vector<Plan> plans(1);
-    int rc = compile_plan(g->hg, *pattern, 1, 0, 1,
+    int rc = compile_user(g, *pattern, 1, 0, 1,
                           FLEXIS_MODE_FULL | FLEXIS_MODE_NO_MNI | FLEXIS_MODE_NO_MIS | FLEXIS_MODE_EXACT_MIS, plans[0]);
     if (rc) return rc;
     flexis_support_result r;
@@ -481,7 +593,8 @@ void flexis_free_pattern_set(flexis_pattern_set *s) { delete s; }
 int flexis_canonical_code(const flexis_pattern *pattern, int32_t *labels_out, uint32_t *bits_out,
                           int32_t *perm_out) {
     if (!pattern || !labels_out || !bits_out) return FLEXIS_E_INVALID;
-    if (pattern->n < 1 || pattern->n > MAXN || pattern->m < 0 || !pattern->labels) return FLEXIS_E_INVALID;
+    if (pattern->n < 1 || pattern->n > MAXN || pattern->m < 0 || !pattern->labels || pattern->edge_labels)
+        return FLEXIS_E_INVALID;
     Pat p;
     p.n = pattern->n;
     for (int i = 0; i < p.n; i++) p.lab[i] = pattern->labels[i];
@@ -662,7 +775,7 @@ int flexis_serve_submit(flexis_server *s, int64_t request_id, const flexis_patte
     flexis_server::Req r;
     r.id = request_id;
     r.t0 = flexis_server::clock::now();
-    int rc = compile_plan(s->g->hg, *pattern, sigma, num, LAMBDA_DEN, mode, r.plan);
+    int rc = compile_user(s->g, *pattern, sigma, num, LAMBDA_DEN, mode, r.plan);
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(s->mu);

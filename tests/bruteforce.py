@@ -289,3 +289,51 @@ def is_candidate(labels, adj, F):
     inF = [in_F(u) for u in range(n)]
     return any(inF[u] and inF[v] for u in range(n) for v in range(u + 1, n)
                if frozenset((u, v)) not in adj)
+
+
+# ----------------------------------------------------------------------------- edge labels
+# Sec. 2.3.5: an edge (u, v) with label l is replaced by edges (u, w), (w, v) through a new vertex
+# w labelled l.  extend_graph / extend_pattern write that transform out; maps_edge_labelled is
+# the direct definition (injective, vertex labels kept, every pattern edge on a data edge with
+# the same edge label) that the transform must reproduce.
+
+def extend_graph(labels, edges, edge_labels):
+    """Extended graph: (labels, edges) with one vertex per kept edge; edge label l becomes label
+    base + l, base = 1 + the largest vertex label.  Self-loops dropped; of repeated vertex pairs
+    the first edge is kept."""
+    base = max(labels) + 1 if len(labels) else 0
+    lab = list(labels)
+    out, seen = [], set()
+    for (a, b), l in zip(edges, edge_labels):
+        if a == b or frozenset((a, b)) in seen:
+            continue
+        seen.add(frozenset((a, b)))
+        w = len(lab)
+        lab.append(base + l)
+        out += [(a, w), (w, b)]
+    return lab, out, base
+
+
+def extend_pattern(labels, edges, edge_labels, base):
+    lab = list(labels)
+    out = []
+    for (a, b), l in zip(edges, edge_labels):
+        w = len(lab)
+        lab.append(base + l)
+        out += [(a, w), (w, b)]
+    return lab, out
+
+
+def maps_edge_labelled(labels, edges, edge_labels, pat_labels, pat_edges, pat_edge_labels):
+    elab = {}
+    for (a, b), l in zip(edges, edge_labels):
+        if a != b and frozenset((a, b)) not in elab:
+            elab[frozenset((a, b))] = l
+    n = len(pat_labels)
+    out = []
+    for f in itertools.permutations(range(len(labels)), n):
+        if any(labels[f[u]] != pat_labels[u] for u in range(n)):
+            continue
+        if all(elab.get(frozenset((f[a], f[b]))) == l for (a, b), l in zip(pat_edges, pat_edge_labels)):
+            out.append(f)
+    return out

@@ -168,14 +168,17 @@ def test_overlap_graph_and_exact_mis_tiny_graphs():
 
 def test_exact_mis_powerlaw_small_overlap_graphs(powerlaw):
     lab, src, dst, _ = powerlaw
-    pats = random_patterns(60, range(3, 6), ["path", "star", "cycle", "clique", "tree"], lab, 151)
+    # overlap graphs small enough for the oracle's exhaustive search: rare-label patterns
+    pats = random_patterns(600, range(2, 6), ["path", "star", "cycle", "clique", "tree"], lab, 151)
     og = oracle.Graph(lab, src, dst)
     small = []
     for pl, pe in pats:
-        got = og.overlap_graph(pl, pe, max_maps=20000, cap_inst=30)
-        if got is not None and len(got[0]) <= 30:
-            small.append((pl, pe, og.max_independent_set(pl, pe, max_maps=20000, max_inst=30), got))
-    assert len(small) >= 5
+        if og.count_maps(pl, pe, cap=5000) >= 5000:
+            continue
+        got = og.overlap_graph(pl, pe, max_maps=5000, cap_inst=30)
+        if got is not None and 2 <= len(got[0]) <= 30:
+            small.append((pl, pe, og.max_independent_set(pl, pe, max_maps=5000, max_inst=30), got))
+    assert len(small) >= 10
     g = fx.Graph(lab, src, dst)
     res = g.support_batch([(pl, pe) for pl, pe, _, _ in small], 60, 0.5, FULL | EXACT | fx.FLEXIS_MODE_NO_MNI)
     for (pl, pe, big, got), r in zip(small, res):

@@ -563,3 +563,38 @@ def test_overlap_graph_and_mis_match_brute_force():
             r = g.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=1)
             # Theorem 1: mIS <= MIS <= n mIS
             assert r["mis"] <= big <= len(pl) * r["mis"]
+
+
+# ----------------------------------------------------------------------------- edge labels
+
+def edge_labelled_cases(count, seed):
+    st = Stream(seed)
+    out = []
+    shapes = ["path", "star", "cycle", "tree"]
+    for _ in range(count):
+        nv = 5 + int(st.integers(1, 4)[0])
+        ne = min(nv * (nv - 1) // 2, nv + int(st.integers(1, nv)[0]))
+        s = int(st.next(1)[0] % (1 << 31))
+        src, dst = erdos_renyi(nv, ne, s)
+        lab = labels_uniform(nv, 2, s + 1)
+        el = [int(x) for x in st.integers(ne, 2)]
+        n = 2 + int(st.integers(1, 2)[0])              # 2..3 vertices, n + m <= 8
+        pe = pattern_edges(shapes[int(st.integers(1, len(shapes))[0])], n, st)
+        pl = [int(x) for x in st.integers(n, 2)]
+        pel = [int(x) for x in st.integers(len(pe), 2)]
+        out.append((lab, src, dst, el, pl, pe, pel, s))
+    return out
+
+
+def test_edge_label_extension_preserves_maps():
+    # the maps of the extended pattern in the extended graph are the edge-label-respecting maps
+    # of the original pattern (one extended map per original map: the graph is simple)
+    for lab, src, dst, el, pl, pe, pel, s in edge_labelled_cases(80, 31):
+        E = list(zip(src.tolist(), dst.tolist()))
+        want = bf.maps_edge_labelled(lab.tolist(), E, el, pl, pe, pel)
+        xl, xe, base = bf.extend_graph(lab.tolist(), E, el)
+        pxl, pxe = bf.extend_pattern(pl, pe, pel, base)
+        g = oracle.Graph(np.asarray(xl, np.int32), np.asarray([a for a, b in xe], np.int32),
+                         np.asarray([b for a, b in xe], np.int32), seed=s)
+        r = g.support(pxl, pxe, sigma=1, lam=1.0, mode="full", tier=0)
+        assert r["n_maps"] == len(want) == g.count_maps(pxl, pxe)
