@@ -223,6 +223,11 @@ typedef struct {
                                  maps extended */
     int64_t enum_scanned;     /* ... label-slice entries scanned by those extensions */
     int64_t enum_bytes;       /* ... algorithmic bytes read by them */
+    int64_t search_scanned;   /* greedy search kernel: label-slice entries scanned as candidates
+                                 (the A of the algorithmic-bytes model) */
+    int64_t search_bound;     /* ... partial maps it bound, each counted with its length (level+1):
+                                 sum over levels i of (i+1) E_i */
+    int64_t search_map_words; /* ... vertex ids of the maps it found and wrote (n per map) */
 } flexis_stats;
 
 const char *flexis_status_string(int status);

@@ -105,7 +105,8 @@ class flexis_stats(C.Structure):
                 ("d2h_bytes", C.c_int64), ("search_ms", C.c_float), ("mni_ms", C.c_float),
                 ("total_ms", C.c_float), ("host_gen_ms", C.c_float), ("host_compile_ms", C.c_float),
                 ("search_launches", C.c_int32), ("batches", C.c_int32), ("graph_launches", C.c_int32),
-                ("enum_rows", C.c_int64), ("enum_scanned", C.c_int64), ("enum_bytes", C.c_int64)]
+                ("enum_rows", C.c_int64), ("enum_scanned", C.c_int64), ("enum_bytes", C.c_int64),
+                ("search_scanned", C.c_int64), ("search_bound", C.c_int64), ("search_map_words", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

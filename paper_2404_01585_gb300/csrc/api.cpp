@@ -83,6 +83,9 @@ void add_stats(flexis_stats &a, const flexis_stats &b) {
     a.enum_rows += b.enum_rows;
     a.enum_scanned += b.enum_scanned;
     a.enum_bytes += b.enum_bytes;
+    a.search_scanned += b.search_scanned;
+    a.search_bound += b.search_bound;
+    a.search_map_words += b.search_map_words;
 }
 
 // Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism

@@ -175,9 +175,15 @@ __device__ __forceinline__ bool check_candidate(const DevGraphView &G, const War
 // found is the first map avoiding the current used set.
 enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
 
+// Counters of the search's algorithmic work (warp-uniform): driver-slice entries scanned, and
+// partial maps bound, each weighted by its length (level + 1).
+struct SearchWork {
+    unsigned long long scanned = 0, bound = 0;
+};
+
 __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                        unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
-                       bool resume) {
+                       bool resume, SearchWork &work) {
     const int lane = threadIdx.x & 31;
     const int n = W.n;
     int i = 1;
@@ -236,6 +242,7 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
             bytes += 4ull * min(32u, hi - pos);
+            work.scanned += min(32u, hi - pos);
             steps++;
             base = pos;
             pos += 32;
@@ -246,6 +253,7 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
         const int32_t c = __ldg(G.adj + base + j);
         if (resume && used && used_bit(used, c)) continue;  // became used since the chunk scan
         if (lane == 0) W.t[i] = c;
+        work.bound += (unsigned)(i + 1);
         if (i == n - 1) {  // keep the position so that a later resume continues past this map
             if (lane == 0) { W.level = i; W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = mask; W.conf[i] = conf; }
             __syncwarp();
@@ -263,7 +271,8 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
 __device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
                                           int32_t root, unsigned long long &bytes, uint32_t &probes,
                                           uint32_t &steps) {
-    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false) == DFS_FOUND;
+    SearchWork work;
+    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false, work) == DFS_FOUND;
 }
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {

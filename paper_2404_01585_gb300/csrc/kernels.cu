@@ -45,7 +45,12 @@ namespace fx {
 // search space is an ordered list of saved sub-searches (the first one's index in the slot's
 // map entry 0, each saved state holding the index of the next); the slot's map is the map of
 // the first sub-search in that order that finds one, once every earlier one has found none.
-enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3 };
+// A LEX slot's root is known to have a map avoiding the used set of an earlier round (its
+// existence check found one); it needs the search for its first map in the greedy order.
+enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3, SLOT_LEX = 4 };
+// phase of a root search: the first map in the greedy order, or the existence check that
+// precedes it for patterns with a cycle (Plan::use_exist)
+enum : int32_t { PHASE_LEX = 0, PHASE_EXIST = 1 };
 // saved sub-search status (word SUSP_STATUS of its saved state); its map in SUSP_MAP..+7
 enum : int32_t { SS_PENDING = 0, SS_NONE = 1, SS_FOUND = 2 };
 constexpr int SPLIT_MAX = 15;  // pieces one split may create
@@ -83,6 +88,9 @@ struct Ctl {
     int32_t pad;
     unsigned long long bytes_greedy;
     unsigned long long bytes_mni;
+    unsigned long long alg_scanned;   // greedy search: driver-slice entries scanned (A)
+    unsigned long long alg_bound;     // greedy search: sum over bound partial maps of their length
+    unsigned long long alg_map_words; // greedy search: words of the maps it wrote (n per map found)
     unsigned long long search_items;
     unsigned long long mni_items;
     unsigned long long mni_total;
@@ -119,7 +127,8 @@ constexpr int DFS_SAVE_STRIDE = 192;  // words per saved sub-search
 constexpr int SUSP_STATUS = DFS_SAVE_WORDS;      // SS_* of the saved sub-search
 constexpr int SUSP_NEXT = DFS_SAVE_WORDS + 1;    // next sub-search of the same slot, or -1
 constexpr int SUSP_MAP = DFS_SAVE_WORDS + 2;     // its map (by level) when SS_FOUND
-static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large");
+constexpr int SUSP_PHASE = SUSP_MAP + MAXN;      // PHASE_* of the sub-search (same for a whole slot)
+static_assert(SUSP_PHASE < DFS_SAVE_STRIDE, "saved search state too large");
 constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
 constexpr uint32_t SEARCH_BUDGET = 4096;  // candidate chunks a root search runs per round
 
@@ -135,6 +144,7 @@ __device__ void reset_ctl(Ctl *c) {
     c->active[0] = c->active[1] = 0;
     c->err = 0;
     c->bytes_greedy = c->bytes_mni = 0;
+    c->alg_scanned = c->alg_bound = c->alg_map_words = 0;
     c->search_items = c->mni_items = 0;
     c->mni_total = c->mni_next = 0;
 }
@@ -191,11 +201,12 @@ __device__ unsigned int claim_sids(unsigned int *m, int want, unsigned int ALL) 
     return 0;
 }
 
-__device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, int status) {
+__device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, int status, int phase) {
     const int lane = threadIdx.x & 31;
     for (int w = lane; w < DFS_SAVE_WORDS; w += 32) dst[w] = reinterpret_cast<const uint32_t *>(&W)[w];
     if (lane == 0) dst[SUSP_STATUS] = status;
     if (status == SS_FOUND && lane < MAXN) dst[SUSP_MAP + lane] = W.t[lane];
+    if (lane == 0) dst[SUSP_PHASE] = (uint32_t)phase;
     __syncwarp();
 }
 
@@ -210,8 +221,9 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     WarpState &W = ws[threadIdx.x >> 5];
     const int n_items = *reinterpret_cast<volatile int32_t *>(&B.ctl->n_items[q]);
     if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->acount[q] = 0;  // list q has been consumed
-    unsigned long long bytes = 0;
+    unsigned long long bytes = 0, map_words = 0;
     uint32_t probes = 0;
+    SearchWork work;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&B.ctl->next_item[q], 1);
@@ -222,20 +234,32 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         const int off = item.y & 0xFFFFFF;
         const int sid_in = (item.y >> 24) - 1;
         const Plan &P = B.plans[p];
-        load_level_plan(W, P.greedy, P);
         const size_t slot = (size_t)p * 2 * B.Wmax + off;
         int32_t *seq = B.win_map + slot * MAXN;
         const int32_t root = B.win_root[slot];
         const uint32_t *used = B.used + (size_t)p * B.G.words;
         uint32_t *sbase = B.susp + (size_t)p * KSUSP * DFS_SAVE_STRIDE;
         const bool resume = sid_in >= 0;
+        // a fresh root of a pattern with a cycle first checks that some map avoiding the used
+        // set exists, in the existence order (the answer does not depend on the order)
+        int phase = resume ? (int)sbase[(size_t)sid_in * DFS_SAVE_STRIDE + SUSP_PHASE]
+                           : (P.use_exist && B.win_state[slot] == SLOT_NEEDS ? PHASE_EXIST : PHASE_LEX);
+        load_level_plan(W, phase == PHASE_EXIST ? P.exist : P.greedy, P);
         if (resume) {
             const uint32_t *src = sbase + (size_t)sid_in * DFS_SAVE_STRIDE;
             for (int w = lane; w < DFS_SAVE_WORDS; w += 32) reinterpret_cast<uint32_t *>(&W)[w] = src[w];
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume);
+        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
+        if (phase == PHASE_EXIST && r == DFS_FOUND && !resume) {
+            // a map exists: search the root's first map in the greedy order right away, with
+            // what is left of the budget
+            phase = PHASE_LEX;
+            load_level_plan(W, P.greedy, P);
+            r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, false, work);
+        }
+        if (r == DFS_FOUND && phase == PHASE_LEX) map_words += (unsigned)P.n;
         int sidA = sid_in;
         if (r == DFS_SUSPENDED) {
             const bool head = !resume || seq[0] == sid_in;
@@ -296,7 +320,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                             }
                         }
                         __syncwarp();
-                        save_state(sbase + (size_t)sid * DFS_SAVE_STRIDE, W, SS_PENDING);
+                        save_state(sbase + (size_t)sid * DFS_SAVE_STRIDE, W, SS_PENDING, phase);
                         if (lane == 0) sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)sid;
                         link = sid;
                     }
@@ -310,7 +334,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                     }
                     __syncwarp();
                 }
-                save_state(sbase + (size_t)sidA * DFS_SAVE_STRIDE, W, SS_PENDING);
+                save_state(sbase + (size_t)sidA * DFS_SAVE_STRIDE, W, SS_PENDING, phase);
                 if (lane == 0) {
                     if (np == 0) sbase[(size_t)sidA * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
                     else sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
@@ -331,13 +355,18 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                 if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
                 if (r == DFS_FOUND && lane < P.n) seq[lane] = W.t[lane];
             } else {  // the state is kept so that the sub-search can go on past its map
-                save_state(sbase + (size_t)sid_in * DFS_SAVE_STRIDE, W, r == DFS_FOUND ? SS_FOUND : SS_NONE);
+                save_state(sbase + (size_t)sid_in * DFS_SAVE_STRIDE, W, r == DFS_FOUND ? SS_FOUND : SS_NONE, phase);
             }
         }
         __syncwarp();
     }
     unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
     if (lane == 0 && tot) atomicAdd(&B.ctl->bytes_greedy, tot);
+    if (lane == 0 && work.scanned) {
+        atomicAdd(&B.ctl->alg_scanned, work.scanned);
+        atomicAdd(&B.ctl->alg_bound, work.bound);
+        atomicAdd(&B.ctl->alg_map_words, map_words);
+    }
 }
 
 
@@ -394,6 +423,23 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         int32_t head = -1, last = -1;
         unsigned int release = 0;
         int32_t cur_sid = sq[0];
+        if (cur_sid >= 0 && sbase[(size_t)cur_sid * DFS_SAVE_STRIDE + SUSP_PHASE] == PHASE_EXIST) {
+            // existence check: one piece finding a map settles it (the slot then needs its first
+            // map in the greedy order); otherwise pieces that found nothing are dropped below
+            bool any = false;
+            unsigned int all = 0;
+            for (int32_t r2 = cur_sid, g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
+                const uint32_t *e = sbase + (size_t)r2 * DFS_SAVE_STRIDE;
+                all |= 1u << r2;
+                any |= e[SUSP_STATUS] == SS_FOUND;
+                r2 = (int32_t)e[SUSP_NEXT];
+            }
+            if (any) {
+                atomicAnd(&S->susp_mask, ~all);
+                const_cast<int32_t *>(st_cur)[s] = SLOT_LEX;
+                continue;
+            }
+        }
         for (int guard = 0; cur_sid >= 0 && guard < KSUSP; guard++) {
             uint32_t *e = sbase + (size_t)cur_sid * DFS_SAVE_STRIDE;
             const int32_t next = (int32_t)e[SUSP_NEXT];
@@ -489,7 +535,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
     // a suspended search, or one that found no room to be suspended and starts over, is
     // undecided: nothing at or after it can be committed yet
     for (int s = tid; s < horizon; s += nthr)
-        if (st_cur[s] == SLOT_SEQ || st_cur[s] == SLOT_NEEDS) atomicMin(&s_f, s);
+        if (st_cur[s] == SLOT_SEQ || st_cur[s] == SLOT_NEEDS || st_cur[s] == SLOT_LEX) atomicMin(&s_f, s);
     __syncthreads();
     const int f = s_f;
     // 4. commit the map slots before f, in slot order
@@ -581,7 +627,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
     auto n_items_of = [&](int s) -> int {
         if (s >= nw) return 0;
         const int st = st_nxt[s];
-        if (st == SLOT_NEEDS) return 1;
+        if (st == SLOT_NEEDS || st == SLOT_LEX) return 1;
         if (st != SLOT_SEQ) return 0;
         int c = 0;
         for (int32_t r2 = mp_nxt[(size_t)s * MAXN], g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
@@ -606,7 +652,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         const int tot = block_scan(nd, excl, sh_scan);
         if (nd) {
             const int o = nxt * Wmax + s;
-            if (st_nxt[s] == SLOT_NEEDS) {
+            if (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_LEX) {
                 B.items[wr + excl] = make_int2(p, o);
             } else {
                 int w = wr + excl;
@@ -1244,6 +1290,9 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
         stats->kernel_launches = launches;
         stats->alg_bytes_greedy = (int64_t)w.h_ctl->bytes_greedy;
         stats->alg_bytes = (int64_t)(w.h_ctl->bytes_greedy + w.h_ctl->bytes_mni);
+        stats->search_scanned = (int64_t)w.h_ctl->alg_scanned;
+        stats->search_bound = (int64_t)w.h_ctl->alg_bound;
+        stats->search_map_words = (int64_t)w.h_ctl->alg_map_words;
         stats->search_launches = search_launches;
         stats->graph_launches = (int32_t)graph_launches;
         stats->d2h_bytes = (int64_t)sizeof(Ctl) * (rounds / R + 1);  // control-word reads

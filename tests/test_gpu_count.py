@@ -166,10 +166,11 @@ def test_overlap_graph_and_exact_mis_tiny_graphs():
     assert seen >= 100
 
 
-def test_exact_mis_powerlaw_small_overlap_graphs(powerlaw):
-    lab, src, dst, _ = powerlaw
-    # overlap graphs small enough for the oracle's exhaustive search: rare-label patterns
-    pats = random_patterns(600, range(2, 6), ["path", "star", "cycle", "clique", "tree"], lab, 151)
+def test_exact_mis_sparse_graph_small_overlap_graphs():
+    # overlap graphs small enough for the oracle's exhaustive search: a sparse graph, many labels
+    lab, src, dst = make_graph(kind="er", nv=3000, ne=5000, nl=6, law="uniform", zipf_s=None,
+                               gamma=None, seed=153)
+    pats = random_patterns(300, range(2, 6), ["path", "star", "cycle", "tree"], lab, 151)
     og = oracle.Graph(lab, src, dst)
     small = []
     for pl, pe in pats:

@@ -598,3 +598,22 @@ def test_edge_label_extension_preserves_maps():
                          np.asarray([b for a, b in xe], np.int32), seed=s)
         r = g.support(pxl, pxe, sigma=1, lam=1.0, mode="full", tier=0)
         assert r["n_maps"] == len(want) == g.count_maps(pxl, pxe)
+
+
+def test_parallel_mining_driver_equals_serial_oracle():
+    # the multi-process driver (all-cores CPU baseline, large parity samples) must return what
+    # the oracle's own serial mining loop returns
+    from oracle.parallel import Pool, mine_parallel
+    cases = mining_cases(6, 77)
+    pool = None
+    try:
+        for lab, src, dst, sigma, lam, max_edges, s in cases:
+            if pool is not None:
+                pool.close()
+            pool = Pool(lab, src, dst, workers=2, seed=s)
+            got = mine_parallel(pool, lab, src, dst, sigma, int(round(lam * 10**6)), max_edges)
+            want = oracle.Graph(lab, src, dst, seed=s).mine(sigma=sigma, lam=lam, max_edges=max_edges)
+            assert got == want
+    finally:
+        if pool is not None:
+            pool.close()
