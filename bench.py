@@ -1,24 +1,29 @@
 #!/usr/bin/env python
 """Benchmark: candidate supports evaluated per second, FLEXIS frequent subgraph mining on GB300.
 
-Workload (one step): the MiCo-shaped mining sweep -- a seeded Chung-Lu graph (exponent 2.3,
-100,000 vertices, 1,080,000 undirected edges, 29 vertex labels Zipf(1.2)); Algorithm 1 mining of
-all connected patterns with up to 5 edges, once per (sigma, lambda) in {1000, 2000, 3000} x
-{0, 0.5, 1}.  Every
-candidate the mining loop evaluates (all levels, all runs) counts as one support evaluation.
+Headline workload (one step): the MiCo-shaped mining sweep -- a seeded Chung-Lu graph
+(exponent 2.3, 100,000 vertices, 1,080,000 undirected edges, 29 vertex labels Zipf(1.2));
+Algorithm 1 mining of all connected patterns with up to 5 edges, once per (sigma, lambda) in
+{1000, 2000, 3000} x {0, 0.5, 1}.  Every candidate the mining loop evaluates (all levels, all
+runs) counts as one support evaluation.
 
   value : supports/s through flexis_mine with the graph already resident on the device
           (CUDA events on the library's stream around the K timed steps; L2 flushed between
           steps by a 256 MiB write).
   e2e   : the same metric through the public API from host buffers: every step loads the graph
           from host arrays (flexis_load_graph), mines, reads the frequent sets back.
-  roofline : the dominant kernel (the greedy search kernel), algorithmic bytes counted by the
-          kernel itself / its summed CUDA-event time, against the measured HBM copy bandwidth.
-  cpu_baseline : the plain C oracle, single thread, on a bounded sample of the same workload.
-  batched_vs_plain : 256 candidates of the sweep evaluated in one batch vs one call each.
-  serving : continuous batching on the YouTube-shaped resident graph (Chung-Lu 2.3, 4.6 M
-          vertices, 43.9 M edges, 80 labels Zipf(1.0)): closed-loop saturated throughput, then
-          Poisson arrivals at 0.3 / 0.6 / 0.9 of it; p50 / p99 latency, 1 s request deadline.
+  roofline : the dominant kernel (the greedy search kernel): algorithmic bytes B counted on the
+          device (4 per label-slice entry scanned, 8 per bound vertex of every partial map -- one
+          write, one read -- and 4 per vertex of every map found) over its summed CUDA-event
+          time, against the measured HBM copy bandwidth; `traffic` is the ncu DRAM bytes per
+          launch of the committed capture (profiles/), null when the kernel source changed since.
+  cpu_baseline : the plain C oracle on a bounded sample of the same workload: all nine runs of
+          the sweep mined to 3 edges on all host cores (candidates spread over processes, each
+          evaluated by the oracle's single-threaded code), and one run on one core; the sample's
+          frequent sets are compared with the GPU's.
+  legs  : the 1 M-vertex batched level (2,000 patterns in one batched pass vs plain one-pattern
+          calls), the Patents-shaped per-level mine, and continuous-batching serving on the
+          YouTube-shaped resident graph at three Poisson arrival rates (p50 / p99).
 
 `python bench.py --impl reference` times the oracle instead (the reference arm of this build is
 its CPU oracle).  N > 1 (torchrun): independent replicas, one per GPU (the evaluation path has no
@@ -44,8 +49,10 @@ SWEEP = [(sigma, lam) for lam in (0.0, 0.5, 1.0) for sigma in (1000, 2000, 3000)
 MAX_EDGES = 5
 METRIC = "candidate supports evaluated/sec (bit-exact vs oracle), batched vs plain on 1 GB300; p50/p99"
 UNIT = "supports/s"
-# oracle sample: the same graph and sweep, mining limited to 3 edges (levels 2..4)
-ORACLE_SAMPLE = dict(runs=[(3000, 0.5), (3000, 1.0)], max_edges=3)
+# oracle samples: the same graph and sweep, mining limited to 3 edges (levels 2..4); all nine runs
+# on all cores, one run on one core
+ORACLE_MAX_EDGES = 3
+ORACLE_SINGLE_RUN = (3000, 0.5)
 
 
 def peaks():
@@ -126,21 +133,34 @@ def config_dict(extra=None):
     return d
 
 
-def run_oracle_sample(lab, src, dst):
-    """The oracle as it stands, single-threaded, on the bounded sample; returns
-    (supports, seconds, description)."""
+def run_oracle_single(lab, src, dst):
+    """The oracle as it stands, one core: one run of the sweep mined to ORACLE_MAX_EDGES.
+    Returns (supports, seconds, description)."""
     import oracle
     oracle.build()
     g = oracle.Graph(lab, src, dst)
+    sigma, lam = ORACLE_SINGLE_RUN
     t0 = time.perf_counter()
-    cand = 0
-    for sigma, lam in ORACLE_SAMPLE["runs"]:
-        _, levels = g.mine(sigma=sigma, lam=lam, max_edges=ORACLE_SAMPLE["max_edges"])
-        cand += sum(c for c, _ in levels.values())
+    _, levels = g.mine(sigma=sigma, lam=lam, max_edges=ORACLE_MAX_EDGES)
     dt = time.perf_counter() - t0
-    desc = (f"oracle tier-1 mining of the same graph, (sigma, lambda) in {ORACLE_SAMPLE['runs']}, "
-            f"max_edges={ORACLE_SAMPLE['max_edges']} (levels 2..4): {cand} supports")
-    return cand, dt, desc
+    cand = sum(c for c, _ in levels.values())
+    return cand, dt, (f"oracle, 1 core: (sigma, lambda) = {ORACLE_SINGLE_RUN} of the sweep mined to "
+                      f"{ORACLE_MAX_EDGES} edges (levels 2..{ORACLE_MAX_EDGES + 1}): {cand} supports")
+
+
+def run_oracle_all_cores(lab, src, dst, pool):
+    """All nine runs of the sweep mined to ORACLE_MAX_EDGES, candidates of each level spread over
+    the pool's processes.  Returns (supports, seconds, description, {run: frequent set})."""
+    from oracle.parallel import mine_parallel
+    t0 = time.perf_counter()
+    cand, sets = 0, {}
+    for sigma, lam in SWEEP:
+        pats, levels = mine_parallel(pool, lab, src, dst, sigma, int(round(lam * 10**6)), ORACLE_MAX_EDGES)
+        cand += sum(c for c, _ in levels.values())
+        sets[(sigma, lam)] = pats
+    dt = time.perf_counter() - t0
+    return cand, dt, (f"oracle on {pool.workers} processes: all nine (sigma, lambda) runs of the sweep mined "
+                      f"to {ORACLE_MAX_EDGES} edges (levels 2..{ORACLE_MAX_EDGES + 1}): {cand} supports"), sets
 
 
 SERVE_SLOTS = 256
@@ -223,28 +243,114 @@ def reduce_over_ranks(dist, ms, count):
     return t_max, c_all, c_all / (t_max / 1e3)
 
 
+def kernel_source_hash():
+    """Hash of the sources of the greedy search kernel (for the ncu traffic figure's validity)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2404_01585_gb300", "csrc")
+    for f in ("kernels.cu", "fx_kern.cuh", "fx.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the search kernel from the committed ncu capture, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_search_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None, d
+    return d.get("dram_bytes_per_launch"), d
+
+
 def reference_arm(args):
+    """The reference arm: the oracle (the reference of this build is a paper with no code), one
+    core, timed on a bounded sample of the headline workload each step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     lab, src, dst = load_inputs()
     for _ in range(args.warmup):
-        run_oracle_sample(lab, src, dst)
+        run_oracle_single(lab, src, dst)
     tot_c, tot_t, desc = 0, 0.0, ""
     for _ in range(args.steps):
-        c, t, desc = run_oracle_sample(lab, src, dst)
+        c, t, desc = run_oracle_single(lab, src, dst)
         tot_c += c
         tot_t += t
     v = tot_c / tot_t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": config_dict({"reference": "plain C oracle (CPU)"}),
+            "data": "synthetic",
+            "config": config_dict({"reference": "plain C oracle (CPU), one core",
+                                   "sample": "each step: " + desc}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_level_leg(fx, local, n_plain=200):
+    """1 M-vertex batched level: 2,000 candidates (trees, cycles, cliques of 3-7 vertices) of a
+    Chung-Lu graph (1 M vertices, 10 M edges, 37 labels Zipf(1.0)) in one batched pass, against
+    plain one-pattern calls (each launched and synchronised on its own) on the first n_plain."""
+    import torch
+    from workloads import batch_level_patterns, make_graph
+    lab, src, dst = make_graph("cl1m")
+    pats = batch_level_patterns(lab, 2000)
+    g = fx.Graph(lab, src, dst, device=local)
+    mode = fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI
+    g.support_batch(pats[:64], 1000, 0.5, mode)  # warm-up
+    ext = torch.cuda.ExternalStream(g.stream(), device=local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ext)
+    t0 = time.perf_counter()
+    res = g.support_batch(pats, 1000, 0.5, mode)
+    e1.record(ext)
+    e1.synchronize()
+    wall_batch = time.perf_counter() - t0
+    ms_batch = e0.elapsed_time(e1)
+    st = g.stats()
+    lat = []
+    for pl, pe in pats[:n_plain]:
+        t1 = time.perf_counter()
+        g.support(pl, pe, 1000, 0.5, mode=mode)
+        lat.append(time.perf_counter() - t1)
+    g.close()
+    lat_sorted = sorted(lat)
+    return {"workload": "2000 candidates, n 3..7, trees/cycles/cliques, sigma=1000, lambda=0.5, EARLY, "
+                        "Chung-Lu gamma=2.3, 1000000 v, 10000000 e, 37 labels Zipf(1.0)",
+            "batched_supports_per_s": len(pats) / (ms_batch / 1e3), "batched_ms": ms_batch,
+            "batched_wall_s": wall_batch, "frequent": int(sum(r["frequent"] for r in res)),
+            "batched_kernel_launches": int(st["kernel_launches"]), "graph_replays": int(st["graph_launches"]),
+            "plain_sample": n_plain, "plain_supports_per_s": n_plain / sum(lat),
+            "plain_p50_ms": 1e3 * lat_sorted[len(lat) // 2],
+            "plain_p99_ms": 1e3 * lat_sorted[min(len(lat) - 1, int(len(lat) * 0.99))]}
+
+
+def patents_leg(fx, local, max_edges):
+    """Patents-shaped per-level mine: Chung-Lu gamma=2.3, 3,774,768 vertices, 16,518,947 edges, 37
+    labels Zipf(1.0); sigma = 20000, lambda = 0.5, memory-admitted batches per level."""
+    from workloads import make_graph
+    lab, src, dst = make_graph("patents")
+    g = fx.Graph(lab, src, dst, device=local)
+    t0 = time.perf_counter()
+    arr, levels = g.mine_arrays(20000, 0.5, max_edges)
+    dt = time.perf_counter() - t0
+    st = g.stats()
+    g.close()
+    cand = sum(c for c, _ in levels.values())
+    return {"workload": f"Patents-shaped mine to {max_edges} edges, sigma=20000, lambda=0.5",
+            "supports": cand, "frequent": int(arr["n"].size), "seconds": dt, "supports_per_s": cand / dt,
+            "levels": {str(k): v for k, v in levels.items()}, "device_ms": st["total_ms"],
+            "batches": int(st["batches"])}
 
 
 def main():
@@ -257,24 +363,33 @@ def main():
     ap.add_argument("--only", default=None,
                     help="SIGMA,LAMBDA: time one mining run instead of the sweep (profiling)")
     ap.add_argument("--skip-extras", action="store_true",
-                    help="skip the e2e, batched-vs-plain and CPU-baseline legs (profiling)")
+                    help="skip the e2e, legs and CPU-baseline parts (profiling)")
+    ap.add_argument("--patents-edges", type=int, default=5,
+                    help="depth of the Patents-shaped leg (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     global SWEEP
     if args.only:
-        s, l = args.only.split(",")
-        SWEEP = [(int(s), float(l))]
+        s_, l_ = args.only.split(",")
+        SWEEP = [(int(s_), float(l_))]
     if args.skip_extras:
         args.no_cpu_baseline = True
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    lab, src, dst = load_inputs()
+    # the oracle's worker processes start before this process touches the GPU (spawn)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle.parallel import Pool
+        pool = Pool(lab, src, dst, workers=os.cpu_count())
 
     import torch
     import paper_2404_01585_gb300 as fx
     import __graft_entry__
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -285,25 +400,24 @@ def main():
     if dist:
         dist.barrier()
 
-    lab, src, dst = load_inputs()
     g = fx.Graph(lab, src, dst, device=local, timing=True)
     ext = torch.cuda.ExternalStream(g.stream(), device=local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 
-    def step():
+    def step(graph, sweep):
         cand, freq = 0, 0
-        acc = {}
-        for sigma, lam in SWEEP:
-            arr, levels = g.mine_arrays(sigma, lam, MAX_EDGES)
+        acc, sets = {}, {}
+        for sigma, lam in sweep:
+            arr, levels = graph.mine_arrays(sigma, lam, MAX_EDGES)
             cand += sum(c for c, _ in levels.values())
             freq += int(arr["n"].size)
-            st = g.stats()
+            st = graph.stats()
             for k, v in st.items():
                 acc[k] = acc.get(k, 0) + v
         return cand, freq, acc
 
     for _ in range(args.warmup):
-        step()
+        step(g, SWEEP)
     flush.zero_()  # the first timed step starts with a cold L2 too (later ones: flush in the loop)
     # timed region
     clocks = Clocks(local)
@@ -319,7 +433,7 @@ def main():
         if k:
             flush.zero_()
             torch.cuda.synchronize()
-        c, f, acc = step()
+        c, f, acc = step(g, SWEEP)
         total_c += c
         for kk, v in acc.items():
             stats[kk] = stats.get(kk, 0) + v
@@ -332,25 +446,29 @@ def main():
     clk = clocks.stop()
     t_max, c_all, value = reduce_over_ranks(dist, ms, total_c)
 
-    # roofline of the greedy search kernel
+    # roofline of the greedy search kernel: algorithmic bytes counted on the device
     peak, peak_kind = peaks()
     search_s = stats["search_ms"] / 1e3
-    achieved = stats["alg_bytes_greedy"] / search_s / 1e9 if search_s > 0 else 0.0
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    launches = max(1, int(stats["search_launches"]))
+    alg_b = 4 * stats["search_scanned"] + 8 * stats["search_bound"] + 4 * stats["search_map_words"]
+    achieved = alg_b / search_s / 1e9 if search_s > 0 else 0.0
+    traffic, tinfo = committed_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_search (greedy root search)", "peak_kind": peak_kind,
-                "search_ms_share": stats["search_ms"] / ms if ms else None}
+                "alg_bytes_per_launch": alg_b / launches, "launches": launches,
+                "avg_launch_ms": stats["search_ms"] / launches,
+                "alg_terms": {"slice_entries_scanned": int(stats["search_scanned"]),
+                              "bound_vertices": int(stats["search_bound"]),
+                              "map_vertices_written": int(stats["search_map_words"])},
+                "touched_bytes_gbs": stats["alg_bytes_greedy"] / search_s / 1e9 if search_s > 0 else 0.0,
+                "search_ms_share": stats["search_ms"] / ms if ms else None,
+                "traffic_source": (tinfo or {}).get("source")}
 
     # e2e through the public API from host buffers: load + mine + read back, every step
+    e2e_steps = 0 if args.skip_extras else max(1, min(args.steps, 2))
     e2e_c, e2e_t, h2d, d2h = 0, 0.0, 0, 0
-    for k in range(0 if args.skip_extras else args.steps):
+    for k in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g2 = fx.Graph(lab, src, dst, device=local)
@@ -360,50 +478,43 @@ def main():
             e2e_c += sum(c for c, _ in levels.values())
             st = g2.stats()
             h2d += st["h2d_bytes"]
-            d2h += st["d2h_bytes"] + 80 * int(arr["n"].size)
+            d2h += st["d2h_bytes"] + 96 * int(arr["n"].size)
         h2d += info["device_bytes"]
         g2.close()
         torch.cuda.synchronize()
         e2e_t += time.perf_counter() - t0
-    e2e = None if args.skip_extras else {
-        "value": e2e_c / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
-        "d2h_bytes_per_step": d2h // args.steps}
+    e2e = None if not e2e_steps else {
+        "value": e2e_c / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+        "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps}
 
-    # batched vs plain on a sample of the sweep's candidates
-    pats, levels = g.mine(2000, 0.5, 4) if not args.skip_extras else ([], {})
-    sample = [(p["labels"], p["edges"]) for p in pats if p["n"] >= 4][:256]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    if sample:
-        g.support_batch(sample, 2000, 0.5, fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI)
-    t_batch = time.perf_counter() - t0
-    lat = []
-    for lb, ed in sample:
-        t1 = time.perf_counter()
-        g.support(lb, ed, 2000, 0.5, mode=fx.FLEXIS_MODE_EARLY | fx.FLEXIS_MODE_NO_MNI)
-        lat.append(time.perf_counter() - t1)
-    lat.sort()
-    bvp = None if not sample else {"sample": f"{len(sample)} frequent 4-5 vertex patterns of sigma=2000, lambda=0.5",
-           "batched_supports_per_s": len(sample) / t_batch,
-           "plain_supports_per_s": len(sample) / sum(lat),
-           "plain_p50_ms": 1e3 * lat[len(lat) // 2], "plain_p99_ms": 1e3 * lat[min(len(lat) - 1, int(len(lat) * 0.99))]}
-
-    serving = None
+    legs = {}
     if rank == 0 and not args.skip_extras:
+        legs["batched_level"] = batched_level_leg(fx, local)
+        if args.patents_edges > 0:
+            legs["patents_mine"] = patents_leg(fx, local, args.patents_edges)
         from workloads import make_graph
         ylab, ysrc, ydst = make_graph("youtube")
         gy = fx.Graph(ylab, ysrc, ydst, device=local, deadline_ms=SERVE_DEADLINE_MS)
-        serving = serving_leg(gy, fx, ylab, nq=1000, per_rate_s=15.0,
-                              graph_name="YouTube-shaped: Chung-Lu gamma=2.3, 4600000 v, 43900000 e, "
-                                         "80 labels Zipf(1.0)")
+        legs["serving"] = serving_leg(gy, fx, ylab, nq=1000, per_rate_s=15.0,
+                                      graph_name="YouTube-shaped: Chung-Lu gamma=2.3, 4600000 v, 43900000 e, "
+                                                 "80 labels Zipf(1.0)")
         gy.close()
         del ylab, ysrc, ydst
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c, t, desc = run_oracle_sample(lab, src, dst)
-        cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": t}
+    if pool is not None:
+        c1, t1, d1 = run_oracle_single(lab, src, dst)
+        cn, tn, dn, sets = run_oracle_all_cores(lab, src, dst, pool)
+        pool.close()
+        # the sample's frequent sets on the GPU, same runs and depth: bit-exact?
+        same = 0
+        for (sigma, lam), want in sets.items():
+            gp, _ = g.mine(sigma, lam, ORACLE_MAX_EDGES)
+            got = sorted((p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in gp)
+            same += int(got == sorted(want))
+        cpu = {"value": cn / tn, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": dn,
+               "seconds": tn, "single_core": {"value": c1 / t1, "cores": 1, "sample": d1, "seconds": t1},
+               "sample_parity": f"{same} of {len(sets)} runs: identical frequent sets (codes, tau, mis, mni)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -414,7 +525,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(stats.get("kernel_launches", 0)),
                 "graph_replays": int(stats.get("graph_launches", 0)), "clocks": clk,
-                "batched_vs_plain": bvp, "serving": serving,
+                "legs": legs,
                 "kernel_time_ms": {"search": stats["search_ms"], "device_total": stats["total_ms"],
                                    "host_candidate_generation": stats["host_gen_ms"],
                                    "host_compile": stats["host_compile_ms"]}}

@@ -120,8 +120,10 @@ typedef struct {
                                 the maps committed so far (a lower bound of their mIS), mni = -1
                                 and frequent = 0 (undecided); flexis_mine then fails with
                                 FLEXIS_E_TIMEOUT.  The limit is checked between rounds of the
-                                greedy phase; the MNI pass of FLEXIS_MODE_FULL is not bounded by
-                                it.  0 = no limit (default). */
+                                greedy phase, and by the MNI kernel itself (device clock) every
+                                few thousand candidate chunks of a search: a pattern whose MNI
+                                count is cut reports FLEXIS_E_TIMEOUT with its final mis and
+                                frequent and mni = -1.  0 = no limit (default). */
     int32_t root_order;      /* greedy root order (Sec. 3.2.2): 0 = by (H(seed, v), v), the seeded
                                 hash order (default); 1 = by vertex id, the order in which the
                                 paper's matcher visits the data vertices (seed unused) */

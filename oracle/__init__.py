@@ -44,6 +44,8 @@ def lib():
             L.or_hash.argtypes = [C.c_uint64, C.c_int64]
             L.or_graph_new.restype = C.c_void_p
             L.or_graph_new.argtypes = [C.c_int64, i32p, C.c_int64, i32p, i32p, C.c_uint64]
+            L.or_graph_new2.restype = C.c_void_p
+            L.or_graph_new2.argtypes = [C.c_int64, i32p, C.c_int64, i32p, i32p, C.c_uint64, C.c_int]
             L.or_graph_free.argtypes = [C.c_void_p]
             L.or_graph_set_root_order.argtypes = [C.c_void_p, C.c_int]
             L.or_graph_arcs.restype = C.c_int64
@@ -127,7 +129,8 @@ class Graph:
 
     DEFAULT_SEED = 0x5EED
 
-    def __init__(self, labels, src, dst, seed: int = DEFAULT_SEED, root_order: str = "hash"):
+    def __init__(self, labels, src, dst, seed: int = DEFAULT_SEED, root_order: str = "hash",
+                 directed: bool = False):
         self.labels = np.ascontiguousarray(labels, dtype=np.int32)
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.dst = np.ascontiguousarray(dst, dtype=np.int32)
@@ -139,7 +142,8 @@ class Graph:
             ne = self.src.size
         self.nv = self.labels.size
         self.seed = seed
-        self._h = lib().or_graph_new(self.nv, self.labels, ne, self.src, self.dst, seed)
+        self.directed = bool(directed)
+        self._h = lib().or_graph_new2(self.nv, self.labels, ne, self.src, self.dst, seed, 1 if directed else 0)
         if root_order not in ("hash", "id"):
             raise ValueError(root_order)
         lib().or_graph_set_root_order(self._h, 1 if root_order == "id" else 0)

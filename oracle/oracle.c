@@ -62,14 +62,19 @@ uint64_t or_hash(uint64_t seed, int64_t r)
 }
 
 /* ------------------------------------------------------------------ data graph (Sec. 2.2)
- * Undirected, simple, vertex-labelled.  Self-loops and repeated edges are dropped.            */
+ * Simple, vertex-labelled; undirected (each edge read both ways, the paper's loader, Sec. 4.1)
+ * or directed (each edge one arc src -> dst: the paper states the problem on directed graphs,
+ * Sec. 2.2).  Self-loops and repeated edges (arcs) are dropped.                               */
 typedef struct {
     int64_t nv;
     int32_t nl;          /* label ids are 0..nl-1 */
     int32_t *rank_of;    /* [nl] rank of a label (R1), -1 if the label has no vertex */
     int32_t *lab;        /* [nv] rank label of each vertex */
     int64_t *off;        /* [nv+1] */
-    int32_t *nbr;        /* neighbours sorted by id */
+    int32_t *nbr;        /* out-neighbours (all neighbours when undirected), sorted by id */
+    int64_t *ioff;       /* directed: [nv+1] */
+    int32_t *inbr;       /* directed: in-neighbours, sorted by id */
+    int directed;
     uint64_t seed;
     int id_order;        /* 1: roots in vertex-id order (no hash key) */
 } or_graph;
@@ -80,12 +85,43 @@ static int cmp_i32(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
-void *or_graph_new(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
-                   const int32_t *dst, uint64_t seed)
+/* sorted, repeat-free rows of a list of (row, value) pairs: off[nv+1], nbr */
+static void build_rows(int64_t nv, int64_t ne, const int32_t *row, const int32_t *val, const int32_t *skip_a,
+                       const int32_t *skip_b, int64_t **off_out, int32_t **nbr_out)
+{
+    int64_t *deg = calloc(nv + 1, sizeof *deg);
+    for (int64_t e = 0; e < ne; e++)
+        if (skip_a[e] != skip_b[e]) deg[row[e]]++;
+    int64_t *start = malloc((nv + 1) * sizeof *start);
+    start[0] = 0;
+    for (int64_t v = 0; v < nv; v++) start[v + 1] = start[v] + deg[v];
+    int32_t *tmp = malloc((start[nv] > 0 ? start[nv] : 1) * sizeof *tmp);
+    int64_t *fill = calloc(nv + 1, sizeof *fill);
+    for (int64_t e = 0; e < ne; e++)
+        if (skip_a[e] != skip_b[e]) tmp[start[row[e]] + fill[row[e]]++] = val[e];
+    int64_t *off = malloc((nv + 1) * sizeof *off);
+    int32_t *nbr = malloc((start[nv] > 0 ? start[nv] : 1) * sizeof *nbr);
+    int64_t k = 0;
+    for (int64_t v = 0; v < nv; v++) {
+        off[v] = k;
+        int32_t *r = tmp + start[v];
+        qsort(r, (size_t)deg[v], sizeof *r, cmp_i32);
+        for (int64_t i = 0; i < deg[v]; i++)
+            if (i == 0 || r[i] != r[i - 1]) nbr[k++] = r[i];
+    }
+    off[nv] = k;
+    free(deg); free(start); free(tmp); free(fill);
+    *off_out = off;
+    *nbr_out = nbr;
+}
+
+void *or_graph_new2(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
+                    const int32_t *dst, uint64_t seed, int directed)
 {
     or_graph *g = calloc(1, sizeof *g);
     g->nv = nv;
     g->seed = seed;
+    g->directed = directed ? 1 : 0;
     int32_t nl = 0;
     for (int64_t v = 0; v < nv; v++)
         if (labels[v] + 1 > nl) nl = labels[v] + 1;
@@ -105,6 +141,11 @@ void *or_graph_new(int64_t nv, const int32_t *labels, int64_t ne, const int32_t 
     g->lab = malloc((nv > 0 ? nv : 1) * sizeof *g->lab);
     for (int64_t v = 0; v < nv; v++) g->lab[v] = g->rank_of[labels[v]];
 
+    if (g->directed) {
+        build_rows(nv, ne, src, dst, src, dst, &g->off, &g->nbr);    /* out-neighbours */
+        build_rows(nv, ne, dst, src, src, dst, &g->ioff, &g->inbr);  /* in-neighbours */
+        return g;
+    }
     /* adjacency lists: both directions, then sort and drop repeats and loops */
     int64_t *deg = calloc(nv + 1, sizeof *deg);
     for (int64_t e = 0; e < ne; e++)
@@ -134,6 +175,12 @@ void *or_graph_new(int64_t nv, const int32_t *labels, int64_t ne, const int32_t 
     return g;
 }
 
+void *or_graph_new(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
+                   const int32_t *dst, uint64_t seed)
+{
+    return or_graph_new2(nv, labels, ne, src, dst, seed, 0);
+}
+
 /* Root-order variant of R4: id_order = 1 visits roots by vertex id, 0 by (H(seed, v), v). */
 void or_graph_set_root_order(void *gp, int id_order)
 {
@@ -144,7 +191,7 @@ void or_graph_free(void *gp)
 {
     or_graph *g = gp;
     if (!g) return;
-    free(g->rank_of); free(g->lab); free(g->off); free(g->nbr); free(g);
+    free(g->rank_of); free(g->lab); free(g->off); free(g->nbr); free(g->ioff); free(g->inbr); free(g);
 }
 
 int64_t or_graph_arcs(void *gp) { return ((or_graph *)gp)->off[((or_graph *)gp)->nv]; }
@@ -154,6 +201,7 @@ int32_t or_graph_rank(void *gp, int32_t label)
     return (label < 0 || label >= g->nl) ? -1 : g->rank_of[label];
 }
 
+/* an edge u - v (undirected) or an arc u -> v (directed) */
 static int adjacent(const or_graph *g, int32_t u, int32_t v)
 {
     int64_t lo = g->off[u], hi = g->off[u + 1];
@@ -165,18 +213,25 @@ static int adjacent(const or_graph *g, int32_t u, int32_t v)
 }
 
 /* ------------------------------------------------------------------ patterns, R2 canonical form
- * A small pattern: n <= 8 vertices, labels lab[n], adjacency matrix adj[n][n].                */
+ * A small pattern: n <= 8 vertices, labels lab[n], adjacency matrix adj[n][n]: symmetric for an
+ * undirected pattern, adj[i][j] = arc i -> j for a directed one.                               */
 typedef struct {
     int n;
+    int directed;
     int32_t lab[OR_MAXN];
     uint8_t adj[OR_MAXN][OR_MAXN];
 } or_pat;
 
-/* code of the pattern read in the vertex order perm[0..n-1] (position p holds vertex perm[p]) */
+/* i and j joined by an edge or an arc either way */
+static int linked(const or_pat *p, int i, int j) { return p->adj[i][j] || p->adj[j][i]; }
+
+/* code of the pattern read in the vertex order perm[0..n-1] (position p holds vertex perm[p]).
+ * Undirected: for j = 1..n-1, i = 0..j-1 the bit "i not adjacent to j".  Directed (R2 for
+ * directed patterns): for each such pair two bits, "no arc i -> j" then "no arc j -> i".       */
 typedef struct {
     int n;
     int32_t lab[OR_MAXN];
-    uint32_t bits;       /* first code bit is the most significant one */
+    uint64_t bits;       /* first code bit is the most significant one */
 } or_code;
 
 static or_code code_of(const or_pat *p, const int *perm)
@@ -185,10 +240,12 @@ static or_code code_of(const or_pat *p, const int *perm)
     memset(&c, 0, sizeof c);
     c.n = p->n;
     for (int i = 0; i < p->n; i++) c.lab[i] = p->lab[perm[i]];
-    uint32_t bits = 0;
+    uint64_t bits = 0;
     for (int j = 1; j < p->n; j++)
-        for (int i = 0; i < j; i++)
+        for (int i = 0; i < j; i++) {
             bits = (bits << 1) | (p->adj[perm[i]][perm[j]] ? 0u : 1u);
+            if (p->directed) bits = (bits << 1) | (p->adj[perm[j]][perm[i]] ? 0u : 1u);
+        }
     c.bits = bits;
     return c;
 }
@@ -232,6 +289,7 @@ static or_pat canonical(const or_pat *p, int *perm_out)
     or_pat q;
     memset(&q, 0, sizeof q);
     q.n = p->n;
+    q.directed = p->directed;
     for (int i = 0; i < p->n; i++) {
         q.lab[i] = p->lab[best_perm[i]];
         for (int j = 0; j < p->n; j++) q.adj[i][j] = p->adj[best_perm[i]][best_perm[j]];
@@ -248,7 +306,7 @@ static int pat_connected(const or_pat *p)
         for (int u = 0; u < p->n; u++)
             if (seen & (1 << u))
                 for (int v = 0; v < p->n; v++)
-                    if (p->adj[u][v] && !(seen & (1 << v))) { seen |= 1 << v; grew = 1; }
+                    if (linked(p, u, v) && !(seen & (1 << v))) { seen |= 1 << v; grew = 1; }
     }
     return seen == (1 << p->n) - 1;
 }
@@ -261,19 +319,27 @@ static int pat_edges(const or_pat *p)
     return m;
 }
 
-/* build from (labels, edge list); returns -1 on a bad edge */
-static int pat_from(or_pat *p, int n, const int32_t *labels, int m, const int32_t *edges)
+/* build from (labels, edge list); a directed pattern takes each edge (a, b) as the arc a -> b.
+ * Returns -1 on a bad edge. */
+static int pat_from_dir(or_pat *p, int n, const int32_t *labels, int m, const int32_t *edges, int directed)
 {
     if (n < 1 || n > OR_MAXN) return -1;
     memset(p, 0, sizeof *p);
     p->n = n;
+    p->directed = directed ? 1 : 0;
     for (int i = 0; i < n; i++) p->lab[i] = labels[i];
     for (int e = 0; e < m; e++) {
         int a = edges[2 * e], b = edges[2 * e + 1];
         if (a < 0 || b < 0 || a >= n || b >= n || a == b) return -1;
-        p->adj[a][b] = p->adj[b][a] = 1;
+        p->adj[a][b] = 1;
+        if (!directed) p->adj[b][a] = 1;
     }
     return 0;
+}
+
+static int pat_from(or_pat *p, int n, const int32_t *labels, int m, const int32_t *edges)
+{
+    return pat_from_dir(p, n, labels, m, edges, 0);
 }
 
 /* exported: canonical code of a pattern whose labels are used as given.
@@ -289,7 +355,7 @@ int or_canonical(int n, const int32_t *labels, int m, const int32_t *edges, int3
     for (int i = 0; i < n; i++) id[i] = i;
     or_code c = code_of(&q, id);
     for (int i = 0; i < n; i++) { out_labels[i] = c.lab[i]; if (out_perm) out_perm[i] = perm[i]; }
-    *out_bits = c.bits;
+    *out_bits = (uint32_t)c.bits;
     return 0;
 }
 
@@ -303,7 +369,7 @@ static void matching_order(const or_pat *q, int first, int *pi)
         for (int v = 0; v < q->n && pick < 0; v++) {
             if (visited & (1 << v)) continue;
             for (int u = 0; u < q->n; u++)
-                if ((visited & (1 << u)) && q->adj[u][v]) { pick = v; break; }
+                if ((visited & (1 << u)) && linked(q, u, v)) { pick = v; break; }
         }
         pi[k] = pick;           /* q is connected, so pick >= 0 */
         visited |= 1 << pick;
@@ -340,6 +406,7 @@ static int is_map(const or_graph *g, const or_pat *q, const int32_t *e)
         for (int j = 0; j < i; j++) {
             if (e[i] == e[j]) return 0;
             if (q->adj[i][j] && !adjacent(g, e[i], e[j])) return 0;
+            if (q->adj[j][i] && !adjacent(g, e[j], e[i])) return 0;
         }
     }
     return 1;
@@ -410,10 +477,15 @@ static int bt_level(bt_state *s, int k)
     int vk = s->pi[k];
     int anchor = -1;
     for (int j = 0; j < k && anchor < 0; j++)
-        if (q->adj[s->pi[j]][vk]) anchor = s->pi[j];
+        if (linked(q, s->pi[j], vk)) anchor = s->pi[j];
     int32_t a = s->e[anchor];
-    for (int64_t t = g->off[a]; t < g->off[a + 1]; t++) {
-        int32_t c = g->nbr[t];
+    /* candidates: out-neighbours of the anchor's image for an arc anchor -> vk (all neighbours
+     * when undirected), else its in-neighbours */
+    const int64_t *off = g->off;
+    const int32_t *nbr = g->nbr;
+    if (g->directed && !q->adj[anchor][vk]) { off = g->ioff; nbr = g->inbr; }
+    for (int64_t t = off[a]; t < off[a + 1]; t++) {
+        int32_t c = nbr[t];
         if (g->lab[c] != q->lab[vk]) continue;
         if (s->used && s->used[c]) continue;
         int ok = 1;
@@ -421,6 +493,7 @@ static int bt_level(bt_state *s, int k)
             int vj = s->pi[j];
             if (s->e[vj] == c) ok = 0;
             else if (q->adj[vj][vk] && !adjacent(g, s->e[vj], c)) ok = 0;
+            else if (q->adj[vk][vj] && !adjacent(g, c, s->e[vj])) ok = 0;
         }
         if (!ok) continue;
         s->e[vk] = c;
@@ -446,7 +519,7 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
     if (n < 2 || n > OR_MAXN || sigma < 1 || lam_den <= 0 || lam_num < 0 || lam_num > lam_den)
         return -1;
     or_pat p;
-    if (pat_from(&p, n, labels, m, edges)) return -1;
+    if (pat_from_dir(&p, n, labels, m, edges, g->directed)) return -1;
     for (int i = 0; i < n; i++) if (labels[i] < 0) return -1;
     if (!pat_connected(&p)) return -1;
     int64_t tau = or_tau(sigma, lam_num, lam_den, n);
@@ -559,7 +632,7 @@ int64_t or_count_maps(void *gp, int n, const int32_t *labels, int m, const int32
 {
     const or_graph *g = gp;
     or_pat p;
-    if (pat_from(&p, n, labels, m, edges) || !pat_connected(&p)) return -1;
+    if (pat_from_dir(&p, n, labels, m, edges, g->directed) || !pat_connected(&p)) return -1;
     for (int i = 0; i < n; i++) {
         int32_t r = (labels[i] >= 0 && labels[i] < g->nl) ? g->rank_of[labels[i]] : -1;
         if (r < 0) return 0;
@@ -604,7 +677,7 @@ static int64_t instances_of(const or_graph *g, int n, const int32_t *labels, int
 {
     *out = NULL;
     or_pat p;
-    if (n < 2 || pat_from(&p, n, labels, m, edges) || !pat_connected(&p)) return -1;
+    if (n < 2 || pat_from_dir(&p, n, labels, m, edges, g->directed) || !pat_connected(&p)) return -1;
     for (int i = 0; i < n; i++) {
         int32_t r = (labels[i] >= 0 && labels[i] < g->nl) ? g->rank_of[labels[i]] : -1;
         if (r < 0) return 0;
@@ -876,7 +949,7 @@ int64_t or_candidates(int count, const int32_t *ns, const int32_t *labels /* cou
         for (int64_t i = 0; i < n; i++) {
             out_n[i] = C.a[i].n;
             for (int j = 0; j < 8; j++) out_lab[8 * i + j] = j < C.a[i].n ? C.a[i].lab[j] : 0;
-            out_bits[i] = C.a[i].bits;
+            out_bits[i] = (uint32_t)C.a[i].bits;
         }
     free(F.a); free(C.a);
     return n <= cap ? n : -n;
@@ -966,7 +1039,7 @@ void or_mined_get(void *rp, int64_t i, int32_t *n, int32_t *lab, uint32_t *bits,
     or_mined *r = rp;
     *n = r->code[i].n;
     for (int j = 0; j < 8; j++) lab[j] = j < r->code[i].n ? r->code[i].lab[j] : 0;
-    *bits = r->code[i].bits;
+    *bits = (uint32_t)r->code[i].bits;
     for (int j = 0; j < 4; j++) res[j] = r->res[4 * i + j];
 }
 

@@ -267,7 +267,8 @@ int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges
     std::unique_ptr<flexis_graph> g(new (std::nothrow) flexis_graph());
     if (!g) return FLEXIS_E_NOMEM;
     if (opt) g->opt = *opt; else flexis_default_options(&g->opt);
-    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1, g->hg);
+    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1, g->hg,
+                              g->opt.directed ? 1 : 0);
     if (rc) return rc;
     rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
     if (rc) return rc;
@@ -295,7 +296,10 @@ int flexis_load_graph_edge_labels(int64_t n_vertices, const int32_t *labels, int
     for (int64_t e = 0; e < n_edges; e++) {
         if (src[e] < 0 || dst[e] < 0 || src[e] >= n_vertices || dst[e] >= n_vertices || edge_labels[e] < 0)
             return FLEXIS_E_INVALID;
-        const uint64_t a = (uint64_t)std::min(src[e], dst[e]), b = (uint64_t)std::max(src[e], dst[e]);
+        // repeated edges: the same vertex pair (undirected), the same ordered pair (directed)
+        const bool dir = opt && opt->directed;
+        const uint64_t a = (uint64_t)(dir ? src[e] : std::min(src[e], dst[e]));
+        const uint64_t b = (uint64_t)(dir ? dst[e] : std::max(src[e], dst[e]));
         key[(size_t)e] = {a << 32 | b, e};
     }
     std::sort(key.begin(), key.end());
@@ -480,6 +484,8 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
                 flexis_pattern_set **out) {
     int64_t num;
     if (!g || !out || sigma < 1 || max_edges < 1 || !lambda_to_q(lambda, &num)) return FLEXIS_E_INVALID;
+    // candidate generation (Algorithms 2-4) is implemented for undirected patterns
+    if (g->hg.directed) return FLEXIS_E_UNSUPPORTED;
     std::unique_ptr<flexis_pattern_set> S(new flexis_pattern_set());
     S->label_of_rank = g->hg.label_of_rank;
     // level 2: edges(G), one candidate per label pair on a data edge
@@ -502,9 +508,11 @@ int flexis_mine(flexis_graph *g, int64_t sigma, double lambda, int32_t max_edges
         // candidates are canonical codes over label ranks already; the metric step of
         // Algorithm 1 needs the mIS decision only (Sec. 3.2.2)
         parallel_chunks((int64_t)C.size(), threads, [&](int64_t lo, int64_t hi) {
-            for (int64_t i = lo; i < hi; i++)
+            for (int64_t i = lo; i < hi; i++) {
                 compile_code(g->hg, C[(size_t)i], sigma, num, LAMBDA_DEN,
                              FLEXIS_MODE_EARLY | FLEXIS_MODE_NO_MNI, plans[(size_t)i]);
+                plans[(size_t)i].decide_only = 1;
+            }
         });
         total.host_compile_ms += ms_since(t0);
         std::vector<flexis_support_result> res(C.size());

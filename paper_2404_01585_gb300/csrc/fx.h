@@ -25,7 +25,11 @@ struct LevelPlan {
     uint8_t injmask[MAXN];
     uint8_t vert[MAXN];
     uint8_t deg[MAXN];     // pattern degree of the vertex bound at level i
+    uint16_t bdir[MAXN];   // directed patterns: 2 bits per backward level j (bits 2j..2j+1): the
+                           // list of the vertex bound at j that holds level i's candidates --
+                           // DIR_OUT (arc j -> i), DIR_IN (arc i -> j) or DIR_MUT (both arcs)
 };
+enum : int { DIR_OUT = 0, DIR_IN = 1, DIR_MUT = 2 };
 
 // Compiled pattern (host pattern compiler output; plain bytes, device readable).
 struct Plan {
@@ -51,7 +55,9 @@ struct Plan {
     int32_t count_maps;             // FLEXIS_MODE_COUNT_MAPS: enumerate and count all maps
     int32_t skip_mis;               // FLEXIS_MODE_NO_MIS: no greedy phase
     int32_t exact_mis;              // FLEXIS_MODE_EXACT_MIS: maximum independent set of the instances
-    int32_t pad_;
+    int32_t decide_only;            // mining: an infrequent pattern may stop as soon as it cannot
+                                    // reach c (its mis is then a lower bound; only frequent
+                                    // patterns are kept)
 };
 static_assert(sizeof(Plan) <= sizeof(flexis_plan), "plan must fit flexis_plan");
 
@@ -71,6 +77,7 @@ struct alignas(32) VRec {
 // Host copy of the data graph layout (built on the host, mirrored on the device).
 struct HostGraph {
     int64_t nv = 0;
+    int32_t directed = 0;               // vrec holds 3 * nv records: out, in and mutual lists
     int32_t nl_ids = 0;                 // label ids 0..nl_ids-1
     int32_t nl = 0;                     // labels present (ranks 0..nl-1)
     std::vector<int32_t> rank_of;       // [nl_ids] rank or -1
@@ -91,13 +98,16 @@ uint64_t root_hash(uint64_t seed, int64_t r);
 
 // host graph construction (graph.cpp)
 int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
-                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &out);
+                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &out,
+                     int directed = 0);
 
 // ------------------------------------------------------------------ patterns (pattern.cpp)
 struct Pat {  // small labelled graph, adjacency as bit rows
     int n = 0;
     int32_t lab[MAXN] = {0};
-    uint8_t adj[MAXN] = {0};  // bit j of adj[i]: i ~ j
+    uint8_t adj[MAXN] = {0};  // bit j of adj[i]: i ~ j (for a directed pattern: an arc either way)
+    uint8_t out[MAXN] = {0};  // directed pattern: bit j of out[i]: arc i -> j
+    bool directed = false;
 };
 
 struct Code {  // canonical code: (n, labels, bits)
@@ -114,6 +124,9 @@ struct CodeHash {
 
 // canonical form: returns the code; perm[p] = vertex of `p` at canonical position p
 Code canonical(const Pat &p, int *perm);
+// canonical vertex order of a directed pattern (see pattern.cpp); *bits gets its 2-bit-per-pair
+// code
+void canonical_directed(const Pat &p, int *perm, uint64_t *bits);
 Pat pat_of_code(const Code &c);
 bool connected(const Pat &p);
 int edge_count(const Pat &p);
@@ -128,6 +141,7 @@ LevelPlan exist_plan(const Pat &q, int first);
 
 // pattern compile: labels as graph label ids
 void fill_plan(const HostGraph &g, const Code &code, Plan &P);
+void fill_plan_pat(const HostGraph &g, const Pat &canonical_pattern, Plan &P);
 int compile_code(const HostGraph &g, const Code &code, int64_t sigma, int64_t lam_num,
                  int64_t lam_den, int mode, Plan &P);
 int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, int64_t lam_num,

@@ -22,6 +22,8 @@ struct DevGraphView {
     const int32_t *lab_vtx;
     int64_t nv;
     int32_t words;  // used-bitmap words per pattern
+    int64_t dstride;  // directed graphs: nv (records of the out, in and mutual lists follow each
+                      // other); undirected: 0 (every direction reads the one neighbour list)
 };
 
 // ------------------------------------------------------------------ warp depth-first search
@@ -45,12 +47,13 @@ __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
     return (__ldcg(used + (v >> 5)) >> (v & 31)) & 1u;
 }
 
-// Slice of v's neighbours carrying rank label `lab` (warp-cooperative: one load of up to 32
-// label runs, ballot on the label).  Returns an empty slice when the label is absent.
-__device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uint32_t lab,
+// Slice of v's neighbours in list `dir` (DIR_OUT / DIR_IN / DIR_MUT) carrying rank label `lab`
+// (warp-cooperative: one load of up to 32 label runs, ballot on the label).  Returns an empty
+// slice when the label is absent.
+__device__ __forceinline__ void find_slice(const DevGraphView &G, int32_t v, uint32_t lab, uint32_t dir,
                                            uint32_t &lo, uint32_t &hi, unsigned long long &bytes) {
     const int lane = threadIdx.x & 31;
-    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec + v));
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(G.vrec + (int64_t)dir * G.dstride + v));
     bytes += 16;
     const uint32_t adj = r.x, run = r.y, nrun = r.w >> 8;
     lo = hi = 0;
@@ -101,7 +104,7 @@ __device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W,
         const int b = __ffs(bm) - 1;
         bm &= bm - 1;
         uint32_t lo, hi;
-        find_slice(G, W.t[b], lab, lo, hi, bytes);
+        find_slice(G, W.t[b], lab, (W.L.bdir[i] >> (2 * b)) & 3u, lo, hi, bytes);
         if (lo == hi) return false;
         const uint32_t len = hi - lo;
         if (len < dlen) {
@@ -268,12 +271,6 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
     }
 }
 
-__device__ __forceinline__ bool dfs_first(const DevGraphView &G, WarpState &W, const uint32_t *used,
-                                          int32_t root, unsigned long long &bytes, uint32_t &probes,
-                                          uint32_t &steps) {
-    SearchWork work;
-    return dfs_run(G, W, used, root, bytes, probes, steps, 0, false, work) == DFS_FOUND;
-}
 
 __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L, const Plan &P) {
     const int lane = threadIdx.x & 31;

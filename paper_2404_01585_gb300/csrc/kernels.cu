@@ -76,6 +76,7 @@ struct PatState {
     int32_t buf;               // current window buffer (0 or 1)
     uint32_t susp_mask;        // saved-search slots in use (KSUSP bits)
     uint32_t cancelled;        // stopped at a deadline before its decision
+    uint32_t mni_cut;          // the MNI pass passed the deadline before this pattern's count
     int32_t ndirty;            // used-bitmap words this pattern made non-zero (listed up to DIRTY_CAP)
 };
 
@@ -95,6 +96,7 @@ struct Ctl {
     unsigned long long mni_items;
     unsigned long long mni_total;
     unsigned long long mni_next;
+    unsigned long long t0_ns;     // device clock at the start of the evaluation (k_init)
 };
 
 struct Batch {
@@ -120,7 +122,15 @@ struct Batch {
     int32_t *alist;               // [2][P] patterns still in their greedy phase (nullable: all)
     uint32_t *susp;               // [P][KSUSP][DFS_SAVE_STRIDE] saved search states
     flexis_support_result *results;
+    unsigned long long deadline_ns;  // > 0: the MNI pass stops this long after ctl->t0_ns
 };
+
+// The device's global nanosecond clock (PTX special register %globaltimer).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 constexpr int DFS_SAVE_WORDS = (int)(offsetof(WarpState, need) / 4);
 constexpr int DFS_SAVE_STRIDE = 192;  // words per saved sub-search
@@ -167,6 +177,7 @@ __device__ void init_slot(const Batch &B, int p) {
 // an active list, the patterns that have a greedy phase form list 0
 __global__ void k_init(Batch B) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) B.ctl->t0_ns = global_ns();
     if (p >= B.P) return;
     init_slot(B, p);
     if (B.alist && B.st[p].phase == PH_GREEDY) B.alist[atomicAdd(&B.ctl->acount[0], 1)] = p;
@@ -676,7 +687,10 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         S->rounds++;
         S->searched += nitems;
         const bool reached = count >= P.cap;
-        const bool exhausted = nw == 0 && cursor >= rend;
+        // every selection to come needs a root of its own: the roots in the window and those not
+        // yet visited bound it; below c the pattern is infrequent, which is all mining asks
+        const bool hopeless = P.decide_only && count + nw + (int64_t)(rend - cursor) < P.cap;
+        const bool exhausted = (nw == 0 && cursor >= rend) || hopeless;
         if (reached || exhausted) {
             S->done = 1;
             S->exhausted = exhausted && !reached;
@@ -751,6 +765,7 @@ __global__ void k_mni_setup(Batch B) {
 }
 
 constexpr int MNI_CHUNK = 8;
+constexpr uint32_t MNI_BUDGET = 4096;  // candidate chunks of an MNI search between deadline checks
 
 // One warp per candidate vertex d of an orbit: does some map send the orbit representative to d?
 __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
@@ -788,8 +803,19 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
             const int32_t d = __ldg(B.G.lab_vtx + P.lab_begin[u] + (int)(c - B.mni_seg[seg]));
             items++;
             uint32_t steps = 0;
-            const bool found = dfs_first(B.G, W, nullptr, d, bytes, probes, steps);
-            if (found && lane == 0) atomicAdd(cnt, 1ull);
+            // existence search in slices of MNI_BUDGET candidate chunks; between slices the
+            // deadline is checked and the search resumes where it stopped
+            SearchWork work;
+            int r = dfs_run(B.G, W, nullptr, d, bytes, probes, steps, MNI_BUDGET, false, work);
+            while (r == DFS_SUSPENDED) {
+                if (B.deadline_ns && global_ns() - B.ctl->t0_ns > B.deadline_ns) {
+                    if (lane == 0) B.st[p].mni_cut = 1u;
+                    break;
+                }
+                steps = 0;
+                r = dfs_run(B.G, W, nullptr, d, bytes, probes, steps, MNI_BUDGET, true, work);
+            }
+            if (r == DFS_FOUND && lane == 0) atomicAdd(cnt, 1ull);
         }
     }
     unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
@@ -890,6 +916,11 @@ __global__ void k_finalize(Batch B) {
             r.status = FLEXIS_E_TIMEOUT;
             r.mni = -1;
             r.frequent = 0;
+        } else if (S.mni_cut && P.want_mni) {
+            // the deadline passed during the MNI pass: mis and frequent are final, mni is not
+            r.status = FLEXIS_E_TIMEOUT;
+            r.mni = -1;
+            r.flags &= ~(uint32_t)FLEXIS_FLAG_MNI_SATURATED;
         }
     }
     B.results[p] = r;
@@ -945,6 +976,7 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
     g->view.lab_vtx = (const int32_t *)g->d_labvtx;
     g->view.nv = hg.nv;
     g->view.words = (int32_t)std::max<int64_t>(1, (hg.nv + 31) / 32);
+    g->view.dstride = hg.directed ? hg.nv : 0;
     g->max_degree = hg.max_degree;
     if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
@@ -1161,6 +1193,7 @@ int dev_eval(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support_resu
     }
     const size_t smem = small_commit ? commit_smem_of<KMAP_SMALL>() : commit_smem(Wmax);
     const int sblocks = search_grid(g, cfg);
+    B.deadline_ns = cfg.deadline_ms > 0 ? (unsigned long long)cfg.deadline_ms * 1000000ull : 0ull;
 
     int64_t launches = 0;
     CK(cudaEventRecord(g->ev[0], stream));
@@ -1439,6 +1472,7 @@ int dev_support_noalloc(DeviceGraph *g, const Plan *h_plan, flexis_support_resul
     B.mni_seg = reinterpret_cast<unsigned long long *>(base + L.mni_seg);
     B.susp = reinterpret_cast<uint32_t *>(base + L.susp);
     B.results = reinterpret_cast<flexis_support_result *>(base + L.result);
+    B.deadline_ns = deadline_ms > 0 ? (unsigned long long)deadline_ms * 1000000ull : 0ull;
     // the scratch keeps the previous call's contents: the used bitmap must start empty (the
     // pattern state and control words are rewritten by k_init)
     CK(cudaMemcpyAsync(base + L.plan, h_plan, sizeof(Plan), cudaMemcpyHostToDevice, stream));

@@ -130,6 +130,60 @@ Code canonical(const Pat &p, int *perm) {
     return c;
 }
 
+// Directed patterns: the code of an order is (labels in order, then for columns j = 1..n-1 and rows
+// i = 0..j-1 two bits: "no arc i -> j", "no arc j -> i"), the canonical order the one with the
+// lexicographically smallest code; positions are filled left to right with the label of each
+// position forced (sorted label multiset) and prefixes that exceed the best code's are pruned.
+namespace {
+struct DCanonSearch {
+    const Pat *p;
+    int n;
+    int32_t slab[MAXN];
+    int perm[MAXN];
+    int best_perm[MAXN];
+    uint64_t best_bits;
+    bool have;
+    int total_bits;
+
+    void rec(int pos, int used, uint64_t bits, int nb) {
+        if (pos == n) {
+            if (!have || bits < best_bits) {
+                best_bits = bits;
+                memcpy(best_perm, perm, sizeof(int) * n);
+                have = true;
+            }
+            return;
+        }
+        for (int w = 0; w < n; w++) {
+            if ((used >> w & 1) || p->lab[w] != slab[pos]) continue;
+            uint64_t b = bits;
+            for (int i = 0; i < pos; i++) {
+                b = (b << 1) | (((p->out[perm[i]] >> w) & 1) ? 0u : 1u);
+                b = (b << 1) | (((p->out[w] >> perm[i]) & 1) ? 0u : 1u);
+            }
+            const int nb2 = nb + 2 * pos;
+            if (have && nb2 > 0 && b > (best_bits >> (total_bits - nb2))) continue;
+            perm[pos] = w;
+            rec(pos + 1, used | (1 << w), b, nb2);
+        }
+    }
+};
+}  // namespace
+
+void canonical_directed(const Pat &p, int *perm, uint64_t *bits) {
+    DCanonSearch s;
+    s.p = &p;
+    s.n = p.n;
+    for (int i = 0; i < p.n; i++) s.slab[i] = p.lab[i];
+    std::sort(s.slab, s.slab + p.n);
+    s.have = false;
+    s.best_bits = 0;
+    s.total_bits = p.n * (p.n - 1);
+    s.rec(0, 0, 0, 0);
+    memcpy(perm, s.best_perm, sizeof(int) * p.n);
+    if (bits) *bits = s.best_bits;
+}
+
 Pat pat_of_code(const Code &c) {
     Pat p;
     p.n = c.n;
@@ -166,6 +220,11 @@ struct AutSearch {
             bool ok = true;
             for (int i = 0; i < pos && ok; i++)
                 if (has(*p, i, pos) != has(*p, img[i], w)) ok = false;
+            if (p->directed)  // arcs keep their direction
+                for (int i = 0; i < pos && ok; i++)
+                    if (((p->out[i] >> pos) & 1) != ((p->out[img[i]] >> w) & 1) ||
+                        ((p->out[pos] >> i) & 1) != ((p->out[w] >> img[i]) & 1))
+                        ok = false;
             if (!ok) continue;
             img[pos] = w;
             rec(pos + 1, used | (1 << w));
@@ -200,10 +259,19 @@ static LevelPlan plan_of_order(const Pat &q, const int *order) {
         L.vert[i] = (uint8_t)order[i];
         L.lab[i] = (uint8_t)q.lab[order[i]];
         uint8_t bm = 0, im = 0;
+        uint16_t bd = 0;
         for (int j = 0; j < i; j++) {
-            if (has(q, order[j], order[i])) bm |= (uint8_t)(1 << j);
+            if (has(q, order[j], order[i])) {
+                bm |= (uint8_t)(1 << j);
+                if (q.directed) {
+                    const bool fwd = (q.out[order[j]] >> order[i]) & 1, back = (q.out[order[i]] >> order[j]) & 1;
+                    const int d = fwd && back ? DIR_MUT : fwd ? DIR_OUT : DIR_IN;
+                    bd |= (uint16_t)(d << (2 * j));
+                }
+            }
             if (q.lab[order[j]] == q.lab[order[i]]) im |= (uint8_t)(1 << j);
         }
+        L.bdir[i] = bd;
         L.bmask[i] = bm;
         L.injmask[i] = im;
         L.deg[i] = (uint8_t)__builtin_popcount(q.adj[order[i]]);
@@ -302,11 +370,13 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
         if (pat.labels[i] < 0) return FLEXIS_E_INVALID;
         p.lab[i] = pat.labels[i];
     }
+    p.directed = g.directed != 0;  // on a directed graph an edge (a, b) is the arc a -> b
     for (int e = 0; e < pat.m; e++) {
         int a = pat.edges[2 * e], b = pat.edges[2 * e + 1];
         if (a < 0 || b < 0 || a >= pat.n || b >= pat.n || a == b) return FLEXIS_E_INVALID;
         p.adj[a] |= (uint8_t)(1 << b);
         p.adj[b] |= (uint8_t)(1 << a);
+        p.out[a] |= (uint8_t)(1 << b);
     }
     if (!connected(p)) return FLEXIS_E_INVALID;
     P.n_edges = edge_count(p);
@@ -325,17 +395,39 @@ int compile_plan(const HostGraph &g, const flexis_pattern &pat, int64_t sigma, i
         }
         p.lab[i] = r;
     }
-    fill_plan(g, canonical(p, nullptr), P);
+    if (!p.directed) {
+        fill_plan(g, canonical(p, nullptr), P);
+        return FLEXIS_OK;
+    }
+    int perm[MAXN];
+    canonical_directed(p, perm, nullptr);
+    Pat q;
+    q.n = p.n;
+    q.directed = true;
+    for (int i = 0; i < p.n; i++) {
+        q.lab[i] = p.lab[perm[i]];
+        for (int j = 0; j < p.n; j++) {
+            if ((p.adj[perm[i]] >> perm[j]) & 1) q.adj[i] |= (uint8_t)(1 << j);
+            if ((p.out[perm[i]] >> perm[j]) & 1) q.out[i] |= (uint8_t)(1 << j);
+        }
+    }
+    P.code_n = q.n;
+    for (int i = 0; i < q.n; i++) P.code_lab[i] = (uint8_t)q.lab[i];
+    P.code_bits = 0;  // directed codes are not reported
+    fill_plan_pat(g, q, P);
     return FLEXIS_OK;
 }
 
 // Matching orders, label slices and (when MNI is wanted) orbit plans of a canonical pattern
 // whose labels are ranks of g.
 void fill_plan(const HostGraph &g, const Code &code, Plan &P) {
-    Pat q = pat_of_code(code);
     P.code_n = code.n;
     for (int i = 0; i < code.n; i++) P.code_lab[i] = (uint8_t)code.lab[i];
     P.code_bits = code.bits;
+    fill_plan_pat(g, pat_of_code(code), P);
+}
+
+void fill_plan_pat(const HostGraph &g, const Pat &q, Plan &P) {
     for (int u = 0; u < q.n; u++) {
         P.cadj[u] = q.adj[u];
         for (int w = 0; w < q.n; w++)

@@ -337,3 +337,22 @@ def maps_edge_labelled(labels, edges, edge_labels, pat_labels, pat_edges, pat_ed
         if all(elab.get(frozenset((f[a], f[b]))) == l for (a, b), l in zip(pat_edges, pat_edge_labels)):
             out.append(f)
     return out
+
+
+# ----------------------------------------------------------------------------- directed graphs
+# Sec. 2.2 states the problem on directed graphs: a map keeps labels, is injective, and sends
+# every pattern arc a -> b to a data arc f(a) -> f(b).
+
+def maps_directed(data_labels, data_arcs, pat_labels, pat_arcs):
+    out_nb = [set() for _ in data_labels]
+    for a, b in data_arcs:
+        if a != b:
+            out_nb[a].add(b)
+    n = len(pat_labels)
+    res = []
+    for f in itertools.permutations(range(len(data_labels)), n):
+        if any(data_labels[f[u]] != pat_labels[u] for u in range(n)):
+            continue
+        if all(f[b] in out_nb[f[a]] for a, b in pat_arcs):
+            res.append(f)
+    return res

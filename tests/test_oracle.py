@@ -617,3 +617,72 @@ def test_parallel_mining_driver_equals_serial_oracle():
     finally:
         if pool is not None:
             pool.close()
+
+
+# ----------------------------------------------------------------------------- directed graphs
+
+def directed_cases(count, seed):
+    st = Stream(seed)
+    out = []
+    for _ in range(count):
+        nv = 5 + int(st.integers(1, 5)[0])
+        na = nv + int(st.integers(1, 2 * nv)[0])
+        s = int(st.next(1)[0] % (1 << 31))
+        src = st.integers(na, nv).astype(np.int32)
+        dst = st.integers(na, nv).astype(np.int32)
+        lab = labels_uniform(nv, 1 + int(st.integers(1, 2)[0]), s + 1)
+        n = 2 + int(st.integers(1, 3)[0])
+        # a random weakly connected pattern: a random tree, each edge oriented at random, plus
+        # a few extra arcs (reciprocal ones included)
+        pe = pattern_edges("tree", n, st)
+        arcs = [(a, b) if st.uniform(1)[0] < 0.5 else (b, a) for a, b in pe]
+        for _ in range(int(st.integers(1, 3)[0])):
+            a, b = (int(x) for x in st.integers(2, n))
+            if a != b and (a, b) not in arcs:
+                arcs.append((a, b))
+        pl = [int(x) for x in st.integers(n, int(lab.max()) + 1)]
+        out.append((lab, src, dst, pl, arcs, s))
+    return out
+
+
+def test_directed_tiers_agree_with_brute_force():
+    for lab, src, dst, pl, arcs, s in directed_cases(100, 41):
+        A = list(zip(src.tolist(), dst.tolist()))
+        M = bf.maps_directed(lab.tolist(), A, pl, arcs)
+        g = oracle.Graph(lab, src, dst, seed=s, directed=True)
+        for sigma, lam in ((1, 1.0), (3, 0.5)):
+            r0 = g.support(pl, arcs, sigma=sigma, lam=lam, mode="full", tier=0, want_selected=True)
+            r1 = g.support(pl, arcs, sigma=sigma, lam=lam, mode="full", tier=1, want_selected=True)
+            assert r0["n_maps"] == len(M) == g.count_maps(pl, arcs)
+            assert (r0["mis"], r0["mni"], r0["selected"]) == (r1["mis"], r1["mni"], r1["selected"])
+            assert r0["mni"] == bf.mni(M, len(pl))
+            assert bf.is_independent(r1["selected"]) and bf.is_maximal(r1["selected"], M)
+
+
+def test_directed_symmetric_graph_counts_equal_undirected():
+    # both arcs of every edge + every pattern edge in both directions: the same maps as the
+    # undirected graph and pattern (|M| and MNI agree; the greedy order need not)
+    for lab, src, dst, pl, pe, s in tiny_cases(60, 43):
+        both_s = np.concatenate([src, dst]).astype(np.int32)
+        both_d = np.concatenate([dst, src]).astype(np.int32)
+        arcs = [(a, b) for a, b in pe] + [(b, a) for a, b in pe]
+        gd = oracle.Graph(lab, both_s, both_d, seed=s, directed=True)
+        gu = oracle.Graph(lab, src, dst, seed=s)
+        rd = gd.support(pl, arcs, sigma=1, lam=1.0, mode="full", tier=0)
+        ru = gu.support(pl, pe, sigma=1, lam=1.0, mode="full", tier=0)
+        assert (rd["n_maps"], rd["mni"]) == (ru["n_maps"], ru["mni"])
+
+
+def test_directed_relabelling_invariance():
+    st = Stream(45)
+    for lab, src, dst, pl, arcs, s in directed_cases(40, 47):
+        g = oracle.Graph(lab, src, dst, seed=s, directed=True)
+        n = len(pl)
+        perm = [int(x) for x in st.permutation(n)]
+        pl2 = [0] * n
+        for u in range(n):
+            pl2[perm[u]] = pl[u]
+        arcs2 = [(perm[a], perm[b]) for a, b in arcs]
+        a = g.support(pl, arcs, sigma=2, lam=0.5, mode="full", tier=1, want_selected=True)
+        b = g.support(pl2, arcs2, sigma=2, lam=0.5, mode="full", tier=1, want_selected=True)
+        assert (a["mis"], a["mni"], a["selected"]) == (b["mis"], b["mni"], b["selected"])
