@@ -59,6 +59,10 @@ def lib():
             L.or_support.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64,
                                      C.c_int64, C.c_int64, C.c_int, C.c_int, i64p, C.c_void_p,
                                      C.c_int64, C.POINTER(C.c_int64)]
+            L.or_support_budget.restype = C.c_int
+            L.or_support_budget.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64,
+                                            C.c_int64, C.c_int64, C.c_int, C.c_int, i64p, C.c_void_p,
+                                            C.c_int64, C.POINTER(C.c_int64), C.c_int64]
             L.or_count_maps.restype = C.c_int64
             L.or_count_maps.argtypes = [C.c_void_p, C.c_int, i32p, C.c_int, i32p, C.c_int64]
             L.or_overlap_graph.restype = C.c_int
@@ -163,9 +167,11 @@ class Graph:
 
     def support(self, labels, edges, sigma: int, lam: float = None, *, lam_num: int = None,
                 lam_den: int = LAMBDA_DEN, mode: str = "early", tier: int = 1,
-                want_selected: bool = False):
+                want_selected: bool = False, budget: int = 0):
         """Support of one pattern.  Returns a dict with tau, mis, mni, n_maps (tier 0), frequent,
-        and (optionally) the selected maps as canonical-vertex-indexed tuples."""
+        and (optionally) the selected maps as canonical-vertex-indexed tuples.  mode "early",
+        "early_nomni" (mni = -1) or "full".  budget > 0: None when the searches try more
+        candidate vertices than that (the pattern is skipped)."""
         if lam_num is None:
             lam_num = lam_q(lam)
         lab, m, e = _pat(labels, edges)
@@ -173,9 +179,11 @@ class Graph:
         sel_cap = 1 << 20 if want_selected else 0
         sel = np.zeros((max(sel_cap, 1), 8), np.int32)
         nsel = C.c_int64()
-        rc = lib().or_support(self._h, lab.size, lab, m, e, sigma, lam_num, lam_den,
-                              1 if mode == "early" else 0, tier, out,
-                              sel.ctypes.data if want_selected else None, sel_cap, C.byref(nsel))
+        mcode = {"full": 0, "early": 1, "early_nomni": 2}[mode]
+        rc = lib().or_support_budget(self._h, lab.size, lab, m, e, sigma, lam_num, lam_den, mcode, tier, out,
+                                     sel.ctypes.data if want_selected else None, sel_cap, C.byref(nsel), budget)
+        if rc == -3:
+            return None
         if rc != 0:
             raise ValueError("invalid pattern or parameters")
         res = dict(tau=int(out[0]), mis=int(out[1]), mni=int(out[2]),

@@ -461,6 +461,9 @@ typedef struct {
     map_list *out;
     int64_t count;
     int64_t count_cap;
+    int64_t *nodes;      /* nullable: candidates tried, shared by every search of one call */
+    int64_t budget;      /* > 0: give up once *nodes passes it (the call is then skipped) */
+    int *aborted;
     int32_t e[OR_MAXN];
 } bt_state;
 
@@ -486,6 +489,7 @@ static int bt_level(bt_state *s, int k)
     if (g->directed && !q->adj[anchor][vk]) { off = g->ioff; nbr = g->inbr; }
     for (int64_t t = off[a]; t < off[a + 1]; t++) {
         int32_t c = nbr[t];
+        if (s->nodes && ++*s->nodes > s->budget) { *s->aborted = 1; return 1; }
         if (g->lab[c] != q->lab[vk]) continue;
         if (s->used && s->used[c]) continue;
         int ok = 1;
@@ -504,16 +508,22 @@ static int bt_level(bt_state *s, int k)
 
 /* ------------------------------------------------------------------ support evaluation
  * out[0..7]: tau, mis, mni, n_maps (tier 0 only, else -1), frequent, n, cap, status.
- * mode 0 = FULL (exact counts), 1 = EARLY (counts capped at c = max(tau, 1)).
+ * mode 0 = FULL (exact counts), 1 = EARLY (counts capped at c = max(tau, 1)), 2 = EARLY without
+ * the MNI count (mni = -1: the metric step of Sec. 3.2.2 computes the mIS only).
  * tier 0 = brute force over V^n with an explicit sorted map list; tier 1 = backtracking.
  * sel_out (nullable, capacity sel_cap maps of 8 ids) receives the selected maps, as
- * canonical-vertex-indexed tuples; *n_sel their number.  canon_out (nullable) receives the
- * canonical labels (rank space) [8] and the permutation input->canonical [8].                  */
-int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edges, int64_t sigma,
-               int64_t lam_num, int64_t lam_den, int mode, int tier, int64_t *out,
-               int32_t *sel_out, int64_t sel_cap, int64_t *n_sel)
+ * canonical-vertex-indexed tuples; *n_sel their number.
+ * budget > 0 (tier 1): give up after that many candidate vertices tried over all searches of the
+ * call and return -3 (the pattern is skipped, nothing is reported).                             */
+int or_support_budget(void *gp, int n, const int32_t *labels, int m, const int32_t *edges, int64_t sigma,
+                      int64_t lam_num, int64_t lam_den, int mode, int tier, int64_t *out,
+                      int32_t *sel_out, int64_t sel_cap, int64_t *n_sel, int64_t budget)
 {
     const or_graph *g = gp;
+    int64_t nodes = 0;
+    int aborted = 0;
+    const int want_mni = mode != 2;
+    if (mode == 2) mode = 1;
     memset(out, 0, 8 * sizeof *out);
     if (n_sel) *n_sel = 0;
     if (n < 2 || n > OR_MAXN || sigma < 1 || lam_den <= 0 || lam_num < 0 || lam_num > lam_den)
@@ -568,6 +578,7 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
         free(seen);
         free(M.a);
         if (mode == 1) { if (mis > cap) mis = cap; if (mni > cap) mni = cap; }
+        if (!want_mni) mni = -1;
     } else {
         /* roots = vertices carrying the label of pi_0, in (H, id) order */
         int64_t nr = 0;
@@ -591,8 +602,11 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
             bt_state s;
             memset(&s, 0, sizeof s);
             s.g = g; s.q = &q; s.pi = pi; s.used = used; s.stop_first = 1;
+            if (budget > 0) { s.nodes = &nodes; s.budget = budget; s.aborted = &aborted; }
             s.e[pi[0]] = r;
-            if (bt_level(&s, 1)) {
+            const int hit = bt_level(&s, 1);
+            if (aborted) break;
+            if (hit) {
                 for (int k = 0; k < n; k++) used[s.e[k]] = 1;
                 if (sel_out && mis < sel_cap) memcpy(sel_out + 8 * mis, s.e, 8 * sizeof(int32_t));
                 mis++;
@@ -602,7 +616,7 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
         /* MNI: for every pattern vertex u and every data vertex d with u's label, is there a map
          * with u -> d?  (matching order rooted at u; stop at the first hit)                   */
         mni = -1;
-        for (int u = 0; u < n; u++) {
+        for (int u = 0; u < n && want_mni && !aborted; u++) {
             int piu[OR_MAXN];
             matching_order(&q, u, piu);
             int64_t f = 0;
@@ -612,18 +626,31 @@ int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edg
                 bt_state s;
                 memset(&s, 0, sizeof s);
                 s.g = g; s.q = &q; s.pi = piu; s.used = NULL; s.stop_first = 1;
+                if (budget > 0) { s.nodes = &nodes; s.budget = budget; s.aborted = &aborted; }
                 s.e[u] = (int32_t)d;
-                if (bt_level(&s, 1)) f++;
+                const int hit = bt_level(&s, 1);
+                if (aborted) break;
+                if (hit) f++;
             }
             if (mni < 0 || f < mni) mni = f;
         }
+        if (!want_mni) mni = -1;
     }
     free(used);
+    if (aborted) return -3;
     out[1] = mis;
     out[2] = mni;
     out[4] = mis >= cap ? 1 : 0;
     if (n_sel) *n_sel = mis < sel_cap ? mis : sel_cap;
     return 0;
+}
+
+int or_support(void *gp, int n, const int32_t *labels, int m, const int32_t *edges, int64_t sigma,
+               int64_t lam_num, int64_t lam_den, int mode, int tier, int64_t *out,
+               int32_t *sel_out, int64_t sel_cap, int64_t *n_sel)
+{
+    return or_support_budget(gp, n, labels, m, edges, sigma, lam_num, lam_den, mode, tier, out, sel_out,
+                             sel_cap, n_sel, 0);
 }
 
 /* count of all maps by backtracking (tier 1), stopping at count_cap if > 0 */
@@ -994,7 +1021,10 @@ static void eval_code(const or_graph *g, const or_code *c, int64_t sigma, int64_
         for (int j = i + 1; j < p.n; j++)
             if (p.adj[i][j]) { edges[2 * m] = i; edges[2 * m + 1] = j; m++; }
     }
-    or_support((void *)g, p.n, labels, m, edges, sigma, ln, ld, 1, 1, o, NULL, 0, NULL);
+    /* the metric step computes the mIS decision (Sec. 3.2.2); for a frequent pattern the MNI,
+     * capped at c, is c (mIS <= MNI), which is what is recorded */
+    or_support((void *)g, p.n, labels, m, edges, sigma, ln, ld, 2, 1, o, NULL, 0, NULL);
+    if (o[4]) o[2] = o[6];
 }
 
 void *or_mine(void *gp, int64_t sigma, int64_t lam_num, int64_t lam_den, int max_edges)

@@ -24,9 +24,9 @@ def _init(labels, src, dst, seed, root_order):
 
 def _eval(chunk):
     out = []
-    for labels, edges, sigma, lam_num, mode in chunk:
-        r = _G.support(labels, edges, sigma=sigma, lam_num=lam_num, mode=mode, tier=1)
-        out.append((r["tau"], r["mis"], r["mni"], r["frequent"]))
+    for labels, edges, sigma, lam_num, mode, budget in chunk:
+        r = _G.support(labels, edges, sigma=sigma, lam_num=lam_num, mode=mode, tier=1, budget=budget)
+        out.append(None if r is None else (r["tau"], r["mis"], r["mni"], r["frequent"]))
     return out
 
 
@@ -40,12 +40,13 @@ class Pool:
                              initargs=(np.asarray(labels, np.int32), np.asarray(src, np.int32),
                                        np.asarray(dst, np.int32), seed, root_order))
 
-    def evaluate(self, items, mode="early"):
-        """items: list of (labels, edges, sigma, lam_num); returns [(tau, mis, mni, frequent)]."""
+    def evaluate(self, items, mode="early", budget=0):
+        """items: list of (labels, edges, sigma, lam_num); returns [(tau, mis, mni, frequent)], None
+        for a pattern whose searches passed `budget` candidate vertices (budget > 0)."""
         if not items:
             return []
         k = max(1, min(256, len(items) // (4 * self.workers) + 1))
-        chunks = [[(list(map(int, l)), [tuple(map(int, e)) for e in E], int(s), int(q), mode)
+        chunks = [[(list(map(int, l)), [tuple(map(int, e)) for e in E], int(s), int(q), mode, int(budget))
                    for l, E, s, q in items[i:i + k]] for i in range(0, len(items), k)]
         out = []
         for part in self.pool.map(_eval, chunks):
@@ -90,10 +91,11 @@ def mine_parallel(pool: Pool, labels, src, dst, sigma, lam_num, max_edges, lam_d
         items = []
         for n, labs, bits in C:
             items.append(([label_of_rank[r] for r in labs], _edges_of(n, bits), sigma, lam_num))
-        res = pool.evaluate(items)
+        res = pool.evaluate(items, mode="early_nomni")
         F = []
         for (n, labs, bits), (tau, mis, mni, freq) in zip(C, res):
             if freq:
+                mni = max(tau, 1)  # mIS <= MNI: a frequent pattern's capped MNI is c
                 F.append((n, labs, bits))
                 found.append((n, tuple(labs), bits, tau, mis, mni))
         levels[k] = (len(C), len(F))

@@ -1,26 +1,42 @@
-"""GPU parity at the benchmark's full sizes, in the launch configuration bench.py times.
+"""GPU parity at the workloads' full sizes, in the launch configuration bench.py times.
 
-* MiCo-shaped graph (100,000 vertices, 1,080,000 edges, 29 labels), sigma = 3000 at lambda = 0.5
-  and lambda = 0: the whole frequent-pattern set of the mining loop up to 3 edges equals the
-  oracle's (exact, every pattern and value); up to 5 edges, a deterministic sample of the
-  frequent patterns is re-evaluated by the oracle.
-* The 1 M-vertex batched level (2,000 trees / cycles / cliques of 3-7 vertices): the oracle
-  re-evaluates the patterns it finishes in seconds (<= 4 vertices); for every pattern the
-  selected maps themselves are checked against properties that hold at any size -- each is a
-  map (injective, label- and edge-preserving), the maps are vertex-disjoint, their number is the
-  reported mis (capped at c), and the decision is mis >= c.
+The oracle runs on all host cores (oracle/parallel.py: candidates spread over spawned processes,
+each evaluated by the oracle's plain single-threaded code).  Every input here comes from the
+seeded generators or from the oracle itself, never from the CUDA path.
+
+* MiCo-shaped graph (100,000 vertices, 1,080,000 edges, 29 labels Zipf(1.2)):
+  - all nine (sigma, lambda) runs of the sweep mined to 3 edges: whole frequent sets equal;
+  - three runs mined to 4 edges (the oracle's candidate generator is a plain predicate filter
+    with linear-time set lookups, so the sigma = 1000 levels beyond are out of its reach):
+    whole frequent sets equal;
+  - sigma = 1000, lambda = 0, the heaviest run: level-5 candidates that the oracle generates from
+    a deterministic sample of its own level-4 frequent set, evaluated on both sides (mis and the
+    decision, and the exact mis of the infrequent ones);
+  - sigma = 3000 mined to 5 edges: a sample of the frequent 5-6-vertex patterns re-evaluated.
+* The 1 M-vertex batched level (2,000 trees / cycles / cliques of 3-7 vertices): every pattern the
+  oracle finishes within a search budget of 2e7 candidate vertices is compared (the skipped ones
+  are counted and bounded); every fourth pattern's selected maps are checked for validity.
+* Patents-shaped graph (3,774,768 vertices, 16,518,947 edges): mining to 2 edges (levels 2-3),
+  whole frequent sets equal.
+* YouTube-shaped serving stream (4.6 M vertices, 43.9 M edges): 120 queries served by the
+  continuous-batching server against the oracle, those the oracle finishes within its budget.
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 import pytest
 
 import oracle
 import paper_2404_01585_gb300 as fx
-from workloads import batch_level_patterns, make_graph
+from oracle.parallel import Pool, mine_parallel
+from workloads import Stream, batch_level_patterns, make_graph, random_patterns
 
 pytestmark = pytest.mark.gpu
-EARLY, NO_MNI = fx.FLEXIS_MODE_EARLY, fx.FLEXIS_MODE_NO_MNI
+EARLY, FULL, NO_MNI = fx.FLEXIS_MODE_EARLY, fx.FLEXIS_MODE_FULL, fx.FLEXIS_MODE_NO_MNI
+SWEEP = [(sigma, lam) for lam in (0.0, 0.5, 1.0) for sigma in (1000, 2000, 3000)]
+BUDGET = 20_000_000
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,33 +45,99 @@ def built():
     __graft_entry__.build()
 
 
+def workers():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
 @pytest.fixture(scope="module")
 def mico():
-    return make_graph("mico")
+    lab, src, dst = make_graph("mico")
+    pool = Pool(lab, src, dst, workers=workers())
+    yield lab, src, dst, pool
+    pool.close()
 
 
-@pytest.mark.parametrize("lam", [0.5, 0.0])
-def test_mico_mining_exact_to_3_edges(mico, lam):
-    lab, src, dst = mico
+def rows(pats):
+    return sorted((p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in pats)
+
+
+def test_mico_all_nine_runs_to_3_edges(mico):
+    lab, src, dst, pool = mico
     g = fx.Graph(lab, src, dst)
+    for sigma, lam in SWEEP:
+        got, glev = g.mine(sigma, lam, 3)
+        want, wlev = mine_parallel(pool, lab, src, dst, sigma, int(round(lam * 10**6)), 3)
+        assert glev == wlev, (sigma, lam)
+        assert rows(got) == sorted(want), (sigma, lam)
+    g.close()
+
+
+@pytest.mark.parametrize("sigma,lam", [(3000, 0.0), (2000, 0.5), (3000, 1.0)])
+def test_mico_runs_to_4_edges(mico, sigma, lam):
+    lab, src, dst, pool = mico
+    g = fx.Graph(lab, src, dst)
+    got, glev = g.mine(sigma, lam, 4)
+    want, wlev = mine_parallel(pool, lab, src, dst, sigma, int(round(lam * 10**6)), 4)
+    assert glev == wlev and 5 in glev
+    assert rows(got) == sorted(want)
+    g.close()
+
+
+def edges_of(n, bits):
+    e, t = [], n * (n - 1) // 2 - 1
+    for b in range(1, n):
+        for a in range(b):
+            if not (bits >> t) & 1:
+                e.append((a, b))
+            t -= 1
+    return e
+
+
+def test_mico_sigma1000_level5_candidates_sampled(mico):
+    # candidates of the heaviest run's level 5, generated by the oracle from a sample of its own
+    # frequent 4-vertex patterns (a candidate of the sample is a candidate of the whole set)
+    lab, src, dst, pool = mico
     og = oracle.Graph(lab, src, dst)
-    got, glev = g.mine(3000, lam, 3)
-    want, wlev = og.mine(sigma=3000, lam=lam, max_edges=3)
-    assert glev == wlev
-    assert [(p["n"], p["code_labels"], p["code_bits"], p["tau"], p["mis"], p["mni"]) for p in got] == want
+    label_of_rank = {og.rank(l): l for l in set(int(x) for x in lab)}
+    want3, _ = mine_parallel(pool, lab, src, dst, 1000, 0, 3)
+    F4 = [p for p in want3 if p[0] == 4]
+    sample = F4[:: max(1, len(F4) // 120)][:120]
+    cand = oracle.candidates([(list(l), edges_of(n, b)) for n, l, b, *_ in sample], max_edges=4)
+    cand = cand[:: max(1, len(cand) // 400)][:400]
+    pats = [([label_of_rank[r] for r in labs], edges_of(n, bits)) for n, labs, bits in cand]
+    assert len(pats) >= 200
+    g = fx.Graph(lab, src, dst)
+    got = g.support_batch(pats, 1000, 0.0, EARLY | NO_MNI)
+    want = pool.evaluate([(l, e, 1000, 0) for l, e in pats], mode="early_nomni")
+    infrequent = []
+    for (pl, pe), r, w in zip(pats, got, want):
+        assert (r["tau"], r["mis"], bool(r["frequent"])) == (w[0], w[1], w[3]), (pl, pe, r, w)
+        if not w[3]:
+            infrequent.append((pl, pe))
+    # exact mIS of the infrequent ones (FULL mode runs the greedy over every root)
+    got_f = g.support_batch(infrequent, 1000, 0.0, FULL | NO_MNI)
+    want_f = pool.evaluate([(l, e, 1000, 0) for l, e in infrequent], mode="full", budget=BUDGET)
+    compared = 0
+    for (pl, pe), r, w in zip(infrequent, got_f, want_f):
+        if w is None:
+            continue
+        assert r["mis"] == w[1], (pl, pe, r, w)
+        compared += 1
+    assert compared >= len(infrequent) // 2
     g.close()
 
 
 @pytest.mark.parametrize("lam", [0.5, 0.0])
 def test_mico_mining_sampled_to_5_edges(mico, lam):
-    lab, src, dst = mico
+    lab, src, dst, _ = mico
     g = fx.Graph(lab, src, dst)
     og = oracle.Graph(lab, src, dst)
     got, levels = g.mine(3000, lam, 5)
     assert levels[6][1] > 0  # the sweep really reaches 6-vertex patterns
     for p in got:
         assert p["mis"] == p["tau"] and p["mni"] == p["tau"]  # frequent: counts capped at tau
-    sample = [p for p in got if p["n"] >= 5][::max(1, len([p for p in got if p["n"] >= 5]) // 12)][:12]
+    big = [p for p in got if p["n"] >= 5]
+    sample = big[:: max(1, len(big) // 12)][:12]
     for p in sample:
         w = og.support(list(p["labels"]), p["edges"], sigma=3000, lam=lam, mode="early", tier=1)
         assert (w["tau"], w["mis"], w["mni"], w["frequent"]) == (p["tau"], p["mis"], p["mni"], True), p
@@ -65,18 +147,38 @@ def test_mico_mining_sampled_to_5_edges(mico, lam):
 @pytest.fixture(scope="module")
 def cl1m():
     lab, src, dst = make_graph("cl1m")
-    return lab, src, dst, batch_level_patterns(lab, 2000)
+    pool = Pool(lab, src, dst, workers=workers())
+    yield lab, src, dst, batch_level_patterns(lab, 2000), pool
+    pool.close()
 
 
 def csr(nv, src, dst):
     a = np.concatenate([src, dst]).astype(np.int64)
     b = np.concatenate([dst, src]).astype(np.int64)
-    key = np.unique(a * nv + b)
-    return key
+    return np.unique(a * nv + b)
 
 
-def test_cl1m_batch_sampled_and_selected_maps_valid(cl1m):
-    lab, src, dst, pats = cl1m
+def test_cl1m_batch_vs_oracle_within_budget(cl1m):
+    lab, src, dst, pats, pool = cl1m
+    g = fx.Graph(lab, src, dst)
+    res = g.support_batch(pats, 1000, 0.5, EARLY | NO_MNI)
+    want = pool.evaluate([(list(pl), [tuple(e) for e in np.asarray(pe).tolist()], 1000, 500000) for pl, pe in pats],
+                         mode="early_nomni", budget=BUDGET)
+    compared = skipped = 0
+    for (pl, pe), r, w in zip(pats, res, want):
+        assert r["status"] == 0
+        if w is None:
+            skipped += 1
+            continue
+        assert (r["tau"], r["mis"], bool(r["frequent"])) == (w[0], w[1], w[3]), (pl, pe, r, w)
+        compared += 1
+    print(f"cl1m batch: {compared} compared, {skipped} over the oracle's budget")
+    assert compared >= 1600
+    g.close()
+
+
+def test_cl1m_selected_maps_valid(cl1m):
+    lab, src, dst, pats, _ = cl1m
     g = fx.Graph(lab, src, dst, record_selected=1024)
     res = g.support_batch(pats, 1000, 0.5, EARLY | NO_MNI)
     nv = lab.size
@@ -89,41 +191,73 @@ def test_cl1m_batch_sampled_and_selected_maps_valid(cl1m):
     lab_rank = rank_of[lab]
     n_checked = 0
     for i, ((pl, pe), r) in enumerate(zip(pats, res)):
-        assert r["status"] == 0
         cap = max(r["tau"], 1)
         assert r["frequent"] == (r["mis"] >= cap) and r["mis"] <= cap
-        if i % 4:  # the selected-map check on every fourth pattern keeps the test short
+        if i % 4:
             continue
         n = len(pl)
         maps = np.asarray(g.selected_maps(i, n, 1024), dtype=np.int64).reshape(-1, n)
         assert maps.shape[0] == min(r["mis"], 1024)
         if maps.size == 0:
             continue
-        # maps are indexed by the vertices of the pattern's canonical form over label ranks
         plan_labels, plan_bits, _ = fx.canonical_code([int(rank_of[int(x)]) for x in pl], pe)
-        # injective and vertex-disjoint across maps
         flat = maps.reshape(-1)
-        assert np.unique(flat).size == flat.size
-        # label preserving, position by position
+        assert np.unique(flat).size == flat.size  # injective and vertex-disjoint across maps
         assert np.all(lab_rank[maps] == np.asarray(plan_labels)[None, :])
-        # edges of the canonical pattern (decoded from its code bits) land on data edges
-        cedges, t = [], n * (n - 1) // 2 - 1
-        for b in range(1, n):
-            for a in range(b):
-                if not (plan_bits >> t) & 1:
-                    cedges.append((a, b))
-                t -= 1
-        for a, b in cedges:
+        for a, b in edges_of(n, plan_bits):
             k = maps[:, a] * nv + maps[:, b]
             pos = np.searchsorted(keys, k)
             assert np.all(pos < keys.size) and np.all(keys[np.minimum(pos, keys.size - 1)] == k)
         n_checked += 1
     assert n_checked > 400
-    # the oracle re-evaluates the small patterns it finishes in seconds
-    og = oracle.Graph(lab, src, dst)
-    small = [i for i, (pl, pe) in enumerate(pats) if len(pl) <= 4][:16]
-    for i in small:
-        pl, pe = pats[i]
-        w = og.support(pl, pe, sigma=1000, lam=0.5, mode="early", tier=1)
-        assert (w["tau"], w["mis"], w["frequent"]) == (res[i]["tau"], res[i]["mis"], res[i]["frequent"]), (pl, pe)
+    g.close()
+
+
+def test_patents_mining_to_2_edges():
+    lab, src, dst = make_graph("patents")
+    pool = Pool(lab, src, dst, workers=workers())
+    try:
+        g = fx.Graph(lab, src, dst)
+        got, glev = g.mine(20000, 0.5, 2)
+        want, wlev = mine_parallel(pool, lab, src, dst, 20000, 500000, 2)
+        assert glev == wlev
+        assert rows(got) == sorted(want)
+        g.close()
+    finally:
+        pool.close()
+
+
+def test_youtube_served_queries_vs_oracle():
+    lab, src, dst = make_graph("youtube")
+    st = Stream(2006)
+    pats = random_patterns(120, range(3, 9), ["tree", "cycle", "clique"], lab, 2005)
+    sig = [int((1000, 5000, 20000)[int(x)]) for x in st.integers(len(pats), 3)]
+    lam = [float((0.0, 0.5, 1.0)[int(x)]) for x in st.integers(len(pats), 3)]
+    pool = Pool(lab, src, dst, workers=workers())
+    try:
+        want = pool.evaluate([(list(pl), [tuple(e) for e in np.asarray(pe).tolist()], s, int(round(l * 10**6)))
+                              for (pl, pe), s, l in zip(pats, sig, lam)], mode="early_nomni", budget=BUDGET)
+    finally:
+        pool.close()
+    g = fx.Graph(lab, src, dst, deadline_ms=5000)
+    srv = fx.Server(g, slots=64)
+    for i, (pl, pe) in enumerate(pats):
+        assert srv.submit(i, pl, pe, sig[i], lam[i], EARLY | NO_MNI) == 0
+    got = {}
+    import time
+    t0 = time.time()
+    while len(got) < len(pats) and time.time() - t0 < 300:
+        for rid, r, _ in srv.poll():
+            got[rid] = r
+        time.sleep(0.01)
+    srv.stop()
+    compared = 0
+    for i in range(len(pats)):
+        r, w = got[i], want[i]
+        if w is None or r["status"] != 0:
+            continue
+        assert (r["tau"], r["mis"], bool(r["frequent"])) == (w[0], w[1], w[3]), (pats[i], r, w)
+        compared += 1
+    print(f"youtube stream: {compared} of {len(pats)} compared")
+    assert compared >= 40
     g.close()
