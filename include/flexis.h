@@ -136,7 +136,11 @@ typedef struct {
     int64_t exact_mis_nodes; /* FLEXIS_MODE_EXACT_MIS: branch-and-bound nodes per pattern (0 = 2^24) */
     int32_t exact_mis_maps;  /* FLEXIS_MODE_EXACT_MIS: largest number of distinct instances whose
                                 overlap graph is searched (0 = 2048, at most 4096) */
-    int32_t reserved[6];
+    int32_t autotune;        /* 0 = default: the first batch of >= 4096 patterns of each size
+                                (power-of-two bucket) times a slice of itself under a few per-round
+                                search budgets and keeps the fastest for the graph; -1 = off (the
+                                built-in table).  Results never depend on it */
+    int32_t reserved[5];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
@@ -230,6 +234,8 @@ typedef struct {
     int64_t search_bound;     /* ... partial maps it bound, each counted with its length (level+1):
                                  sum over levels i of (i+1) E_i */
     int64_t search_map_words; /* ... vertex ids of the maps it found and wrote (n per map) */
+    int32_t autotune_probes;  /* slice evaluations the autotuner timed in this call */
+    int32_t search_budget;    /* per-round search budget of the last batch (tuned or table) */
 } flexis_stats;
 
 const char *flexis_status_string(int status);

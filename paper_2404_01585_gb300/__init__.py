@@ -58,7 +58,7 @@ class flexis_options(C.Structure):
                 ("graphs", C.c_int32), ("deadline_ms", C.c_int32), ("root_order", C.c_int32),
                 ("directed", C.c_int32), ("maps_cap", C.c_int64),
                 ("frontier_rows", C.c_int64), ("exact_mis_nodes", C.c_int64),
-                ("exact_mis_maps", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("exact_mis_maps", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class flexis_pattern(C.Structure):
@@ -106,7 +106,8 @@ class flexis_stats(C.Structure):
                 ("total_ms", C.c_float), ("host_gen_ms", C.c_float), ("host_compile_ms", C.c_float),
                 ("search_launches", C.c_int32), ("batches", C.c_int32), ("graph_launches", C.c_int32),
                 ("enum_rows", C.c_int64), ("enum_scanned", C.c_int64), ("enum_bytes", C.c_int64),
-                ("search_scanned", C.c_int64), ("search_bound", C.c_int64), ("search_map_words", C.c_int64)]
+                ("search_scanned", C.c_int64), ("search_bound", C.c_int64), ("search_map_words", C.c_int64),
+                ("autotune_probes", C.c_int32), ("search_budget", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -231,7 +232,7 @@ class Graph:
     Keyword options are the fields of flexis_options: seed, device, window_min, window_max,
     search_blocks, record_selected, search_budget, split_pieces, sub_searches, timing, graphs,
     deadline_ms, root_order, directed, maps_cap, frontier_rows, exact_mis_nodes,
-    exact_mis_maps (meanings in include/flexis.h).  They apply to every
+    exact_mis_maps, autotune (meanings in include/flexis.h).  They apply to every
     call on the graph and to servers started on it."""
 
     def __init__(self, labels, src, dst, edge_labels=None, **options):

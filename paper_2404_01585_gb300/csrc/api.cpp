@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <thread>
@@ -20,6 +21,7 @@ struct flexis_graph {
     int64_t n_input_vertices = 0;  // vertices the caller passed
     int32_t edge_label_base = -1;  // label of edge label 0 in the extended graph; -1: none
     int64_t input_self_loops = 0, input_duplicates = 0;  // of the caller's edge list
+    std::map<int, int32_t> tuned_budget;  // autotuner: per-round search budget per batch-size bucket
 };
 
 struct flexis_pattern_set {
@@ -86,6 +88,8 @@ void add_stats(flexis_stats &a, const flexis_stats &b) {
     a.search_scanned += b.search_scanned;
     a.search_bound += b.search_bound;
     a.search_map_words += b.search_map_words;
+    a.autotune_probes += b.autotune_probes;
+    if (b.search_budget) a.search_budget = b.search_budget;
 }
 
 // Autotuner of the launch shape, by batch size: many patterns -> small windows (parallelism
@@ -133,6 +137,69 @@ void enum_config(const flexis_graph *g, const Plan *plans, int64_t n, EvalConfig
     c.exact_mis_nodes = g->opt.exact_mis_nodes;
 }
 
+// Measured autotuner of the per-round search budget (how far a root search runs before it is
+// suspended, resumed or split): on the first batch of a size bucket (power of two of the pattern
+// count, >= TUNE_MIN) a slice of the batch is evaluated under each candidate budget, the fastest
+// (device time) is kept for the graph and used for the rest of that batch and every later batch
+// of the bucket.  All budgets give the same results, so the slice's results are kept as well.
+constexpr int32_t TUNE_MIN = 4096;
+constexpr int32_t TUNE_CANDIDATES[3] = {1024, 4096, 16384};
+
+int tune_bucket(int64_t P) {
+    int b = 0;
+    while ((1ll << (b + 1)) <= P) b++;
+    return b;
+}
+
+// Evaluate plans [lo, lo + cnt) with the autotuner's budget for the bucket (tuning it first if
+// the bucket is new).  Returns the results into out + lo.
+int eval_chunk(flexis_graph *g, std::vector<Plan> &plans, int64_t lo, int32_t cnt, flexis_support_result *out,
+               flexis_stats &total) {
+    EvalConfig c2 = config_for(g, cnt);
+    enum_config(g, plans.data() + lo, cnt, c2);
+    const bool tunable = g->opt.autotune >= 0 && g->opt.search_budget == 0 && cnt >= TUNE_MIN && !c2.exact_mis;
+    int64_t done = 0;
+    if (tunable) {
+        const int bucket = tune_bucket(cnt);
+        auto it = g->tuned_budget.find(bucket);
+        if (it == g->tuned_budget.end()) {
+            const int32_t slice = std::max<int32_t>(512, std::min<int32_t>(cnt / 8, 8192));
+            float best_ms = 0.f;
+            int32_t best = 0;
+            for (int32_t cand : TUNE_CANDIDATES) {
+                EvalConfig c3 = config_for(g, slice);
+                enum_config(g, plans.data() + lo, slice, c3);
+                c3.search_budget = cand;
+                c3.w_min = c2.w_min;
+                c3.w_max = c2.w_max;
+                flexis_stats st{};
+                int rc = dev_eval_host(g->dg, plans.data() + lo, slice, out + lo, c3, &st);
+                if (rc) return rc;
+                st.patterns = slice;
+                st.autotune_probes = 1;
+                add_stats(total, st);
+                if (best == 0 || st.total_ms < best_ms) {
+                    best_ms = st.total_ms;
+                    best = cand;
+                }
+            }
+            it = g->tuned_budget.emplace(bucket, best).first;
+            done = slice;  // every candidate gave these results
+        }
+        c2.search_budget = it->second;
+    }
+    if (done < cnt) {
+        flexis_stats st{};
+        int rc = dev_eval_host(g->dg, plans.data() + lo + done, (int32_t)(cnt - done), out + lo + done, c2, &st);
+        if (rc) return rc;
+        st.patterns = cnt - done;
+        st.batches = 1;
+        st.search_budget = c2.search_budget ? c2.search_budget : 4096;
+        add_stats(total, st);
+    }
+    return FLEXIS_OK;
+}
+
 // Memory-admitted batches: the device workspace of one batch (used bitmaps, windows, items) is
 // bounded by a share of the free device memory; larger candidate sets run as several batches.
 int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result *out) {
@@ -149,14 +216,8 @@ int eval_plans(flexis_graph *g, std::vector<Plan> &plans, flexis_support_result 
     flexis_stats total{};
     for (int64_t lo = 0; lo < P; lo += chunk) {
         const int32_t cnt = (int32_t)std::min(chunk, P - lo);
-        EvalConfig c2 = config_for(g, cnt);
-        enum_config(g, plans.data() + lo, cnt, c2);
-        flexis_stats st{};
-        int rc = dev_eval_host(g->dg, plans.data() + lo, cnt, out + lo, c2, &st);
+        int rc = eval_chunk(g, plans, lo, cnt, out, total);
         if (rc) return rc;
-        st.patterns = cnt;
-        st.batches = 1;
-        add_stats(total, st);
     }
     g->last = total;
     return FLEXIS_OK;

@@ -355,3 +355,22 @@ def test_large_batch_active_list():
         g = fx.Graph(lab, src, dst, **opts)
         check_batch(g, og, pats, 20, 0.5, EARLY)
         g.close()
+
+
+def test_autotuner_results_identical_and_cached(powerlaw):
+    # the measured autotuner times slices of a large batch under several search budgets; any
+    # budget gives the same results, and the choice is kept for later batches of the same size
+    lab, src, dst, _ = powerlaw
+    pats = random_patterns(4500, range(2, 7), SHAPES, lab, 97)
+    off = fx.Graph(lab, src, dst, autotune=-1)
+    want = [key(r) for r in off.support_batch(pats, 60, 0.5, EARLY | fx.FLEXIS_MODE_NO_MNI)]
+    assert off.stats()["autotune_probes"] == 0
+    off.close()
+    g = fx.Graph(lab, src, dst)
+    first = [key(r) for r in g.support_batch(pats, 60, 0.5, EARLY | fx.FLEXIS_MODE_NO_MNI)]
+    st = g.stats()
+    assert st["autotune_probes"] == 3 and st["search_budget"] in (1024, 4096, 16384)
+    second = [key(r) for r in g.support_batch(pats, 60, 0.5, EARLY | fx.FLEXIS_MODE_NO_MNI)]
+    assert g.stats()["autotune_probes"] == 0 and g.stats()["search_budget"] == st["search_budget"]
+    assert first == want and second == want
+    g.close()
