@@ -397,12 +397,16 @@ int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count
 /* ------------------------------------------------------------------ serving
  * A server keeps the graph resident and evaluates support requests as they arrive
  * (continuous batching): requests are admitted into device slots while earlier ones are still
- * being evaluated, and share the device rounds with them.  Admission is bounded by `slots`
- * and by the estimated device memory of a request.  The graph's options.deadline_ms, when set,
- * bounds each request from its submission: a request past it is reported with status
- * FLEXIS_E_TIMEOUT (see flexis_options).  window_min / window_max / search_budget of the
- * graph's options, when set, replace the server's own defaults (start window 32, at most 2048,
- * 256 candidate chunks per search and round).                                                   */
+ * being evaluated, and share the device rounds with them.  A slot (used-vertex bitmap, window,
+ * state: the device memory one request holds) is the admission unit; slots <= 0 sizes the
+ * server from a quarter of the free device memory.  Two lanes, each with its own slots, CUDA
+ * stream and host thread, run side by side: requests start in the light lane (256 candidate
+ * chunks per search and round); one still searching after 12 rounds is restarted in the heavy
+ * lane (a quarter as many slots, 4096 chunks per round), so long searches do not slow the rounds
+ * of short requests.  The graph's options.deadline_ms, when set, bounds each request from its
+ * submission: a request past it is reported with status FLEXIS_E_TIMEOUT (see flexis_options).
+ * window_min / window_max / search_budget of the graph's options, when set, replace the
+ * server's own defaults (start window 32, at most 2048).                                      */
 int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out);
 /* Queue a request; copies the pattern.  FLEXIS_E_BUSY if the host queue is full. */
 int flexis_serve_submit(flexis_server *s, int64_t request_id, const flexis_pattern *pattern,
