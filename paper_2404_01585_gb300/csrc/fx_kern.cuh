@@ -181,7 +181,7 @@ enum : int { DFS_NONE = 0, DFS_FOUND = 1, DFS_SUSPENDED = 2, DFS_NOROOM = 3 };
 // Counters of the search's algorithmic work (warp-uniform): driver-slice entries scanned, and
 // partial maps bound, each weighted by its length (level + 1).
 struct SearchWork {
-    unsigned long long scanned = 0, bound = 0;
+    uint32_t scanned = 0, bound = 0;  // per search: at most budget x 32 entries
 };
 
 __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
@@ -244,8 +244,7 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
             if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes, rej);
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
-            bytes += 4ull * min(32u, hi - pos);
-            work.scanned += min(32u, hi - pos);
+            work.scanned += min(32u, hi - pos);  // 4 bytes each, added to the touched bytes at the end
             steps++;
             base = pos;
             pos += 32;

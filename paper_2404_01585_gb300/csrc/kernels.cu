@@ -232,10 +232,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     WarpState &W = ws[threadIdx.x >> 5];
     const int n_items = *reinterpret_cast<volatile int32_t *>(&B.ctl->n_items[q]);
     if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->acount[q] = 0;  // list q has been consumed
-    unsigned long long bytes = 0, map_words = 0;
+    unsigned long long bytes = 0, map_words = 0, scanned_all = 0, bound_all = 0;
     uint32_t probes = 0;
-    SearchWork work;
     for (;;) {
+        SearchWork work;
         int it = 0;
         if (lane == 0) it = atomicAdd(&B.ctl->next_item[q], 1);
         it = __shfl_sync(FULLMASK, it, 0);
@@ -262,15 +262,20 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
-        if (phase == PHASE_EXIST && r == DFS_FOUND && !resume) {
+        int r;
+        for (bool again = true; again;) {
+            r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
             // a map exists: search the root's first map in the greedy order right away, with
             // what is left of the budget
-            phase = PHASE_LEX;
-            load_level_plan(W, P.greedy, P);
-            r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, false, work);
+            again = phase == PHASE_EXIST && r == DFS_FOUND && !resume;
+            if (again) {
+                phase = PHASE_LEX;
+                load_level_plan(W, P.greedy, P);
+            }
         }
         if (r == DFS_FOUND && phase == PHASE_LEX) map_words += (unsigned)P.n;
+        scanned_all += work.scanned;
+        bound_all += work.bound;
         int sidA = sid_in;
         if (r == DFS_SUSPENDED) {
             const bool head = !resume || seq[0] == sid_in;
@@ -371,11 +376,11 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         }
         __syncwarp();
     }
-    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
+    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes + 4ull * scanned_all : 0ull);
     if (lane == 0 && tot) atomicAdd(&B.ctl->bytes_greedy, tot);
-    if (lane == 0 && work.scanned) {
-        atomicAdd(&B.ctl->alg_scanned, work.scanned);
-        atomicAdd(&B.ctl->alg_bound, work.bound);
+    if (lane == 0 && scanned_all) {
+        atomicAdd(&B.ctl->alg_scanned, scanned_all);
+        atomicAdd(&B.ctl->alg_bound, bound_all);
         atomicAdd(&B.ctl->alg_map_words, map_words);
     }
 }
@@ -774,7 +779,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
     WarpState &W = ws[threadIdx.x >> 5];
     const unsigned long long total = *reinterpret_cast<volatile unsigned long long *>(&B.ctl->mni_total);
     const int nseg = B.P * MAXN;
-    unsigned long long bytes = 0, items = 0;
+    unsigned long long bytes = 0, items = 0, scanned_all = 0;
     uint32_t probes = 0;
     int cur_seg = -1;
     for (;;) {
@@ -815,10 +820,11 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_mni(Batch B) {
                 steps = 0;
                 r = dfs_run(B.G, W, nullptr, d, bytes, probes, steps, MNI_BUDGET, true, work);
             }
+            scanned_all += work.scanned;
             if (r == DFS_FOUND && lane == 0) atomicAdd(cnt, 1ull);
         }
     }
-    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes : 0ull);
+    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes + 4ull * scanned_all : 0ull);
     if (lane == 0) {
         if (tot) atomicAdd(&B.ctl->bytes_mni, tot);
         if (items) atomicAdd(&B.ctl->mni_items, items);

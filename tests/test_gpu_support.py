@@ -249,11 +249,15 @@ def test_deadline_stops_undecided_patterns_only(powerlaw):
     # one-root windows make every pattern take a round per root, so a 1 ms limit passes while
     # many patterns are undecided; the decided ones keep their exact values
     lab, src, dst, pats = powerlaw
+    # a pattern whose label is absent is decided before any round: one that always finishes
+    pats = list(pats) + [([int(lab.max()) + 5, 0], [(0, 1)])]
+    NO_MNI = fx.FLEXIS_MODE_NO_MNI
     g0 = fx.Graph(lab, src, dst)
-    ref = g0.support_batch(pats, 60, 0.5, EARLY)
+    ref = g0.support_batch(pats, 60, 0.5, EARLY | NO_MNI)
+    ref_full = g0.support_batch(pats, 60, 0.5, FULL)
     g0.close()
     g = fx.Graph(lab, src, dst, window_min=1, window_max=32, deadline_ms=1)
-    res = g.support_batch(pats, 60, 0.5, EARLY)
+    res = g.support_batch(pats, 60, 0.5, EARLY | NO_MNI)
     stopped = 0
     for r, w in zip(res, ref):
         if r["status"] == fx.FLEXIS_E_TIMEOUT:
@@ -262,6 +266,14 @@ def test_deadline_stops_undecided_patterns_only(powerlaw):
         else:
             assert r["status"] == 0 and key(r) == key(w)
     assert 0 < stopped < len(pats)
+    # the MNI pass checks the deadline too: a pattern stopped there keeps its final mis and
+    # decision (only mni is missing); one stopped in its greedy phase is undecided
+    for r, w in zip(g.support_batch(pats, 60, 0.5, FULL), ref_full):
+        if r["status"] == fx.FLEXIS_E_TIMEOUT:
+            assert r["mni"] == -1
+            assert (r["mis"], r["frequent"]) == (w["mis"], w["frequent"]) or (r["mis"] <= w["mis"] and not r["frequent"])
+        else:
+            assert key(r) == key(w)
     with pytest.raises(fx.FlexisError) as e:
         g.mine(30, 0.5, 4)
     assert e.value.code == fx.FLEXIS_E_TIMEOUT
