@@ -41,6 +41,11 @@ struct WarpState {
     LevelPlan L;
     int32_t n;
     int32_t pad[1];
+    // slice cache: the slice of level i's candidates in the list of the vertex bound at level b
+    // depends on that vertex only (label and list are fixed by the plan), so it is looked up
+    // once per vertex bound there; sc_v[i][b] is the vertex it was looked up for (-1: none)
+    int32_t sc_v[MAXN][MAXN];
+    uint32_t sc_lo[MAXN][MAXN], sc_hi[MAXN][MAXN];
 };
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {
@@ -104,7 +109,17 @@ __device__ __forceinline__ bool enter_level(const DevGraphView &G, WarpState &W,
         const int b = __ffs(bm) - 1;
         bm &= bm - 1;
         uint32_t lo, hi;
-        find_slice(G, W.t[b], lab, (W.L.bdir[i] >> (2 * b)) & 3u, lo, hi, bytes);
+        if (W.sc_v[i][b] == W.t[b]) {
+            lo = W.sc_lo[i][b];
+            hi = W.sc_hi[i][b];
+        } else {
+            find_slice(G, W.t[b], lab, (W.L.bdir[i] >> (2 * b)) & 3u, lo, hi, bytes);
+            if (lane == 0) {
+                W.sc_lo[i][b] = lo;
+                W.sc_hi[i][b] = hi;
+                W.sc_v[i][b] = W.t[b];
+            }
+        }
         if (lo == hi) return false;
         const uint32_t len = hi - lo;
         if (len < dlen) {
@@ -277,6 +292,8 @@ __device__ __forceinline__ void load_level_plan(WarpState &W, const LevelPlan &L
     if (lane < WORDS) reinterpret_cast<uint32_t *>(&W.L)[lane] = reinterpret_cast<const uint32_t *>(&L)[lane];
     if (lane < MAXN) W.need[lane] = P.need[lane];
     if (lane == 0) W.n = P.n;
+    // a new plan: no cached slice is valid
+    for (int k = lane; k < MAXN * MAXN; k += 32) (&W.sc_v[0][0])[k] = -1;
     __syncwarp();
 }
 
