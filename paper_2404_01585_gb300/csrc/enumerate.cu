@@ -149,9 +149,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_extend(EnumPass E) {
             if (lane == 0) E.cnt[r] = 0;
             continue;
         }
-        // every map is listed, so any matching order will do: the existence order, which closes
-        // cycles before enumerating a second neighbour of the start
-        load_level_plan(W, P.exist, P);
+        load_level_plan(W, P.greedy, P);
         if (lane >= 1 && lane <= j) W.t[lane - 1] = x;
         __syncwarp();
         rows++;

@@ -50,8 +50,6 @@ struct Plan {
     int32_t want_mni;               // 0 under FLEXIS_MODE_NO_MNI
     int32_t lab_begin[MAXN], lab_end[MAXN];  // label-index slice of each canonical vertex's label
     uint64_t need[MAXN];            // rank labels (< 64) of each canonical vertex's neighbours
-    LevelPlan exist;                // existence-search order rooted at canonical vertex 0
-    int32_t use_exist;              // root searches start with an existence check in that order
     int32_t count_maps;             // FLEXIS_MODE_COUNT_MAPS: enumerate and count all maps
     int32_t skip_mis;               // FLEXIS_MODE_NO_MIS: no greedy phase
     int32_t exact_mis;              // FLEXIS_MODE_EXACT_MIS: maximum independent set of the instances
@@ -136,8 +134,6 @@ void automorphisms(const Pat &p, std::vector<std::array<int8_t, MAXN>> *out, siz
 void orbits(const Pat &p, int *orb);
 // matching order rooted at `first` over canonical pattern q
 LevelPlan level_plan(const Pat &q, int first);
-// matching order for existence searches rooted at `first` (see pattern.cpp)
-LevelPlan exist_plan(const Pat &q, int first);
 
 // pattern compile: labels as graph label ids
 void fill_plan(const HostGraph &g, const Code &code, Plan &P);

@@ -45,12 +45,7 @@ namespace fx {
 // search space is an ordered list of saved sub-searches (the first one's index in the slot's
 // map entry 0, each saved state holding the index of the next); the slot's map is the map of
 // the first sub-search in that order that finds one, once every earlier one has found none.
-// A LEX slot's root is known to have a map avoiding the used set of an earlier round (its
-// existence check found one); it needs the search for its first map in the greedy order.
-enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3, SLOT_LEX = 4 };
-// phase of a root search: the first map in the greedy order, or the existence check that
-// precedes it for patterns with a cycle (Plan::use_exist)
-enum : int32_t { PHASE_LEX = 0, PHASE_EXIST = 1 };
+enum : int32_t { SLOT_NEEDS = 0, SLOT_MAP = 1, SLOT_NONE = 2, SLOT_SEQ = 3 };
 // saved sub-search status (word SUSP_STATUS of its saved state); its map in SUSP_MAP..+7
 enum : int32_t { SS_PENDING = 0, SS_NONE = 1, SS_FOUND = 2 };
 constexpr int SPLIT_MAX = 15;  // pieces one split may create
@@ -137,8 +132,7 @@ constexpr int DFS_SAVE_STRIDE = 192;  // words per saved sub-search
 constexpr int SUSP_STATUS = DFS_SAVE_WORDS;      // SS_* of the saved sub-search
 constexpr int SUSP_NEXT = DFS_SAVE_WORDS + 1;    // next sub-search of the same slot, or -1
 constexpr int SUSP_MAP = DFS_SAVE_WORDS + 2;     // its map (by level) when SS_FOUND
-constexpr int SUSP_PHASE = SUSP_MAP + MAXN;      // PHASE_* of the sub-search (same for a whole slot)
-static_assert(SUSP_PHASE < DFS_SAVE_STRIDE, "saved search state too large");
+static_assert(SUSP_MAP + MAXN <= DFS_SAVE_STRIDE, "saved search state too large");
 constexpr int KSUSP = 32;             // saved sub-searches a pattern may hold at once
 constexpr uint32_t SEARCH_BUDGET = 4096;  // candidate chunks a root search runs per round
 
@@ -212,12 +206,11 @@ __device__ unsigned int claim_sids(unsigned int *m, int want, unsigned int ALL) 
     return 0;
 }
 
-__device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, int status, int phase) {
+__device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, int status) {
     const int lane = threadIdx.x & 31;
     for (int w = lane; w < DFS_SAVE_WORDS; w += 32) dst[w] = reinterpret_cast<const uint32_t *>(&W)[w];
     if (lane == 0) dst[SUSP_STATUS] = status;
     if (status == SS_FOUND && lane < MAXN) dst[SUSP_MAP + lane] = W.t[lane];
-    if (lane == 0) dst[SUSP_PHASE] = (uint32_t)phase;
     __syncwarp();
 }
 
@@ -251,29 +244,15 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         const uint32_t *used = B.used + (size_t)p * B.G.words;
         uint32_t *sbase = B.susp + (size_t)p * KSUSP * DFS_SAVE_STRIDE;
         const bool resume = sid_in >= 0;
-        // a fresh root of a pattern with a cycle first checks that some map avoiding the used
-        // set exists, in the existence order (the answer does not depend on the order)
-        int phase = resume ? (int)sbase[(size_t)sid_in * DFS_SAVE_STRIDE + SUSP_PHASE]
-                           : (P.use_exist && B.win_state[slot] == SLOT_NEEDS ? PHASE_EXIST : PHASE_LEX);
-        load_level_plan(W, phase == PHASE_EXIST ? P.exist : P.greedy, P);
+        load_level_plan(W, P.greedy, P);
         if (resume) {
             const uint32_t *src = sbase + (size_t)sid_in * DFS_SAVE_STRIDE;
             for (int w = lane; w < DFS_SAVE_WORDS; w += 32) reinterpret_cast<uint32_t *>(&W)[w] = src[w];
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r;
-        for (bool again = true; again;) {
-            r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
-            // a map exists: search the root's first map in the greedy order right away, with
-            // what is left of the budget
-            again = phase == PHASE_EXIST && r == DFS_FOUND && !resume;
-            if (again) {
-                phase = PHASE_LEX;
-                load_level_plan(W, P.greedy, P);
-            }
-        }
-        if (r == DFS_FOUND && phase == PHASE_LEX) map_words += (unsigned)P.n;
+        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
+        if (r == DFS_FOUND) map_words += (unsigned)P.n;
         scanned_all += work.scanned;
         bound_all += work.bound;
         int sidA = sid_in;
@@ -336,7 +315,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                             }
                         }
                         __syncwarp();
-                        save_state(sbase + (size_t)sid * DFS_SAVE_STRIDE, W, SS_PENDING, phase);
+                        save_state(sbase + (size_t)sid * DFS_SAVE_STRIDE, W, SS_PENDING);
                         if (lane == 0) sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)sid;
                         link = sid;
                     }
@@ -350,7 +329,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                     }
                     __syncwarp();
                 }
-                save_state(sbase + (size_t)sidA * DFS_SAVE_STRIDE, W, SS_PENDING, phase);
+                save_state(sbase + (size_t)sidA * DFS_SAVE_STRIDE, W, SS_PENDING);
                 if (lane == 0) {
                     if (np == 0) sbase[(size_t)sidA * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
                     else sbase[(size_t)link * DFS_SAVE_STRIDE + SUSP_NEXT] = (uint32_t)old_next;
@@ -371,7 +350,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
                 if (lane == 0) B.win_state[slot] = r == DFS_FOUND ? SLOT_MAP : SLOT_NONE;
                 if (r == DFS_FOUND && lane < P.n) seq[lane] = W.t[lane];
             } else {  // the state is kept so that the sub-search can go on past its map
-                save_state(sbase + (size_t)sid_in * DFS_SAVE_STRIDE, W, r == DFS_FOUND ? SS_FOUND : SS_NONE, phase);
+                save_state(sbase + (size_t)sid_in * DFS_SAVE_STRIDE, W, r == DFS_FOUND ? SS_FOUND : SS_NONE);
             }
         }
         __syncwarp();
@@ -439,23 +418,6 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         int32_t head = -1, last = -1;
         unsigned int release = 0;
         int32_t cur_sid = sq[0];
-        if (cur_sid >= 0 && sbase[(size_t)cur_sid * DFS_SAVE_STRIDE + SUSP_PHASE] == PHASE_EXIST) {
-            // existence check: one piece finding a map settles it (the slot then needs its first
-            // map in the greedy order); otherwise pieces that found nothing are dropped below
-            bool any = false;
-            unsigned int all = 0;
-            for (int32_t r2 = cur_sid, g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
-                const uint32_t *e = sbase + (size_t)r2 * DFS_SAVE_STRIDE;
-                all |= 1u << r2;
-                any |= e[SUSP_STATUS] == SS_FOUND;
-                r2 = (int32_t)e[SUSP_NEXT];
-            }
-            if (any) {
-                atomicAnd(&S->susp_mask, ~all);
-                const_cast<int32_t *>(st_cur)[s] = SLOT_LEX;
-                continue;
-            }
-        }
         for (int guard = 0; cur_sid >= 0 && guard < KSUSP; guard++) {
             uint32_t *e = sbase + (size_t)cur_sid * DFS_SAVE_STRIDE;
             const int32_t next = (int32_t)e[SUSP_NEXT];
@@ -551,7 +513,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
     // a suspended search, or one that found no room to be suspended and starts over, is
     // undecided: nothing at or after it can be committed yet
     for (int s = tid; s < horizon; s += nthr)
-        if (st_cur[s] == SLOT_SEQ || st_cur[s] == SLOT_NEEDS || st_cur[s] == SLOT_LEX) atomicMin(&s_f, s);
+        if (st_cur[s] == SLOT_SEQ || st_cur[s] == SLOT_NEEDS) atomicMin(&s_f, s);
     __syncthreads();
     const int f = s_f;
     // 4. commit the map slots before f, in slot order
@@ -643,7 +605,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
     auto n_items_of = [&](int s) -> int {
         if (s >= nw) return 0;
         const int st = st_nxt[s];
-        if (st == SLOT_NEEDS || st == SLOT_LEX) return 1;
+        if (st == SLOT_NEEDS) return 1;
         if (st != SLOT_SEQ) return 0;
         int c = 0;
         for (int32_t r2 = mp_nxt[(size_t)s * MAXN], g2 = 0; r2 >= 0 && g2 < KSUSP; g2++) {
@@ -668,7 +630,7 @@ __device__ __forceinline__ void commit_one(const Batch &B, int q, int p, int32_t
         const int tot = block_scan(nd, excl, sh_scan);
         if (nd) {
             const int o = nxt * Wmax + s;
-            if (st_nxt[s] == SLOT_NEEDS || st_nxt[s] == SLOT_LEX) {
+            if (st_nxt[s] == SLOT_NEEDS) {
                 B.items[wr + excl] = make_int2(p, o);
             } else {
                 int w = wr + excl;

