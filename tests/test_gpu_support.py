@@ -230,7 +230,7 @@ def test_serving_alone_equals_mixed(powerlaw):
     import time
     got = {}
     for i, (pl, pe) in enumerate(pats):
-        assert srv.submit(i, pl, pe, 60, 0.5) == 0
+        assert srv.submit(i, pl, pe, 60, 0.5, EARLY | NO_MNI) == 0
         if i % 7 == 0:
             time.sleep(0.002)
         for rid, r, lat in srv.poll():
@@ -280,7 +280,7 @@ def test_deadline_stops_undecided_patterns_only(powerlaw):
     # served requests: the limit runs from submission
     srv = fx.Server(g, slots=8)
     for i, (pl, pe) in enumerate(pats[:24]):
-        assert srv.submit(i, pl, pe, 60, 0.5) == 0
+        assert srv.submit(i, pl, pe, 60, 0.5, EARLY | NO_MNI) == 0
     got, t0 = {}, time.time()
     while len(got) < 24 and time.time() - t0 < 120:
         for rid, r, lat in srv.poll():
