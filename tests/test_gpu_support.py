@@ -230,7 +230,7 @@ def test_serving_alone_equals_mixed(powerlaw):
     import time
     got = {}
     for i, (pl, pe) in enumerate(pats):
-        assert srv.submit(i, pl, pe, 60, 0.5, EARLY | NO_MNI) == 0
+        assert srv.submit(i, pl, pe, 60, 0.5) == 0
         if i % 7 == 0:
             time.sleep(0.002)
         for rid, r, lat in srv.poll():
