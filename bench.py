@@ -254,9 +254,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
-    """DRAM bytes per launch of the search kernel from the committed ncu capture, if it was taken on
-    the current kernel source; else None."""
+def committed_traffic(alg_bytes_per_launch):
+    """DRAM bytes per launch of the search kernel, from the committed ncu capture of a small case
+    (DRAM bytes per algorithmic byte there, times this run's algorithmic bytes per launch), if
+    the capture was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "k_search_traffic.json")
     try:
         with open(path) as f:
@@ -265,7 +266,7 @@ def committed_traffic():
         return None, None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None, d
-    return d.get("dram_bytes_per_launch"), d
+    return d["dram_bytes_per_alg_byte"] * alg_bytes_per_launch, d
 
 
 def reference_arm(args):
@@ -452,7 +453,7 @@ def main():
     launches = max(1, int(stats["search_launches"]))
     alg_b = 4 * stats["search_scanned"] + 8 * stats["search_bound"] + 4 * stats["search_map_words"]
     achieved = alg_b / search_s / 1e9 if search_s > 0 else 0.0
-    traffic, tinfo = committed_traffic()
+    traffic, tinfo = committed_traffic(alg_b / launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_search (greedy root search)", "peak_kind": peak_kind,
