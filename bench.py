@@ -462,7 +462,6 @@ def main():
                 "alg_terms": {"slice_entries_scanned": int(stats["search_scanned"]),
                               "bound_vertices": int(stats["search_bound"]),
                               "map_vertices_written": int(stats["search_map_words"])},
-                "touched_bytes_gbs": stats["alg_bytes_greedy"] / search_s / 1e9 if search_s > 0 else 0.0,
                 "search_ms_share": stats["search_ms"] / ms if ms else None,
                 "traffic_source": (tinfo or {}).get("source")}
 

@@ -209,9 +209,11 @@ typedef struct {
     int64_t search_items;     /* root searches run by the search kernel */
     int64_t mni_items;        /* existence searches run by the MNI kernel */
     int64_t kernel_launches;  /* kernels launched by the call */
-    int64_t alg_bytes;        /* algorithmic bytes read by the search kernels (adjacency entries,
-                                 label-run entries, vertex records, used-bitmap words) */
-    int64_t alg_bytes_greedy; /* part of alg_bytes read by the greedy search kernel */
+    int64_t alg_bytes;        /* algorithmic bytes of the search kernels: the greedy search's
+                                 (below) plus the MNI searches' touched bytes (adjacency entries,
+                                 label-run entries, vertex records) */
+    int64_t alg_bytes_greedy; /* greedy search kernel: 4 * search_scanned + 8 * search_bound +
+                                 4 * search_map_words */
     int64_t patterns;         /* patterns evaluated by the call */
     int64_t h2d_bytes;        /* bytes copied host -> device (plans) */
     int64_t d2h_bytes;        /* bytes copied device -> host (results, control words) */
@@ -399,11 +401,10 @@ int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count
  * (continuous batching): requests are admitted into device slots while earlier ones are still
  * being evaluated, and share the device rounds with them.  A slot (used-vertex bitmap, window,
  * state: the device memory one request holds) is the admission unit; slots <= 0 sizes the
- * server from a quarter of the free device memory.  Two lanes, each with its own slots, CUDA
- * stream and host thread, run side by side: requests start in the light lane (256 candidate
- * chunks per search and round); one still searching after 12 rounds is restarted in the heavy
- * lane (a quarter as many slots, 4096 chunks per round), so long searches do not slow the rounds
- * of short requests.  The graph's options.deadline_ms, when set, bounds each request from its
+ * server from a quarter of the free device memory.  Two lanes, each with `slots` slots, its own
+ * CUDA stream and host thread, run side by side: requests start in the light lane; one still
+ * searching after 12 rounds is restarted in the heavy lane, so long searches do not slow the
+ * rounds of short requests (256 candidate chunks per search and round in both).  The graph's options.deadline_ms, when set, bounds each request from its
  * submission: a request past it is reported with status FLEXIS_E_TIMEOUT (see flexis_options).
  * window_min / window_max / search_budget of the graph's options, when set, replace the
  * server's own defaults (start window 32, at most 2048).                                      */

@@ -726,12 +726,11 @@ int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count
 #include <mutex>
 
 // Two lanes, each a device session with its own slots, stream and host thread: every request
-// starts in the light lane (small per-round search budget, so rounds stay short); one still in
-// its greedy phase after LIGHT_STEPS rounds is stopped there and restarted in the heavy lane
-// (larger budget, fewer slots), so that requests needing long searches stop setting the pace of
-// the rounds every light request waits for.  Results do not depend on the lane.
+// starts in the light lane; one still in its greedy phase after LIGHT_STEPS rounds is stopped
+// there and restarted in the heavy lane, so that requests needing long searches stop setting the
+// pace of the rounds every light request waits for (both lanes' rounds run side by side on the
+// device).  Results do not depend on the lane.
 constexpr int LIGHT_STEPS = 12;
-constexpr int32_t HEAVY_BUDGET = 4096;
 
 struct flexis_server {
     using clock = std::chrono::steady_clock;
@@ -860,12 +859,11 @@ int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out) {
     light.slots = slots;
     light.queue = &s->pending;
     light.evict_after = LIGHT_STEPS;
-    heavy.slots = std::max<int32_t>(4, slots / 4);
+    heavy.slots = slots;
     heavy.queue = &s->heavy;
     int rc = serve_create(g->dg, light.slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &light.sess);
     if (rc) return rc;
-    rc = serve_create(g->dg, heavy.slots, g->opt.window_min, g->opt.window_max,
-                      g->opt.search_budget ? g->opt.search_budget : HEAVY_BUDGET, &heavy.sess);
+    rc = serve_create(g->dg, heavy.slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &heavy.sess);
     if (rc) {
         serve_destroy(light.sess);
         return rc;

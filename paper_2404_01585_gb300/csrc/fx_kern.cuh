@@ -46,6 +46,8 @@ struct WarpState {
     // once per vertex bound there; sc_v[i][b] is the vertex it was looked up for (-1: none)
     int32_t sc_v[MAXN][MAXN];
     uint32_t sc_lo[MAXN][MAXN], sc_hi[MAXN][MAXN];
+    // per-warp totals of the algorithmic work (kept by lane 0, out of the registers)
+    unsigned long long acc_scanned, acc_bound, acc_maps;
 };
 
 __device__ __forceinline__ bool used_bit(const uint32_t *used, int32_t v) {

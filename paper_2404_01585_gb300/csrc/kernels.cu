@@ -225,10 +225,13 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     WarpState &W = ws[threadIdx.x >> 5];
     const int n_items = *reinterpret_cast<volatile int32_t *>(&B.ctl->n_items[q]);
     if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->acount[q] = 0;  // list q has been consumed
-    unsigned long long bytes = 0, map_words = 0, scanned_all = 0, bound_all = 0;
-    uint32_t probes = 0;
+    if (lane == 0) W.acc_scanned = W.acc_bound = W.acc_maps = 0;
     for (;;) {
         SearchWork work;
+        // the search's touched-bytes counts are not kept here (the algorithmic bytes are):
+        // unused, the compiler drops them from the hot loop
+        unsigned long long bytes = 0;
+        uint32_t probes = 0;
         int it = 0;
         if (lane == 0) it = atomicAdd(&B.ctl->next_item[q], 1);
         it = __shfl_sync(FULLMASK, it, 0);
@@ -252,9 +255,11 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         }
         uint32_t steps = 0;
         int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
-        if (r == DFS_FOUND) map_words += (unsigned)P.n;
-        scanned_all += work.scanned;
-        bound_all += work.bound;
+        if (lane == 0) {
+            W.acc_scanned += work.scanned;
+            W.acc_bound += work.bound;
+            if (r == DFS_FOUND) W.acc_maps += (unsigned)P.n;
+        }
         int sidA = sid_in;
         if (r == DFS_SUSPENDED) {
             const bool head = !resume || seq[0] == sid_in;
@@ -355,12 +360,12 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         }
         __syncwarp();
     }
-    unsigned long long tot = warp_sum((unsigned long long)probes * 4ull) + (lane == 0 ? bytes + 4ull * scanned_all : 0ull);
-    if (lane == 0 && tot) atomicAdd(&B.ctl->bytes_greedy, tot);
-    if (lane == 0 && scanned_all) {
-        atomicAdd(&B.ctl->alg_scanned, scanned_all);
-        atomicAdd(&B.ctl->alg_bound, bound_all);
-        atomicAdd(&B.ctl->alg_map_words, map_words);
+    if (lane == 0 && W.acc_scanned) {
+        // algorithmic bytes: 4 per slice entry scanned, 8 per bound vertex, 4 per map vertex
+        atomicAdd(&B.ctl->bytes_greedy, 4ull * W.acc_scanned + 8ull * W.acc_bound + 4ull * W.acc_maps);
+        atomicAdd(&B.ctl->alg_scanned, W.acc_scanned);
+        atomicAdd(&B.ctl->alg_bound, W.acc_bound);
+        atomicAdd(&B.ctl->alg_map_words, W.acc_maps);
     }
 }
 
