@@ -401,10 +401,8 @@ int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count
  * (continuous batching): requests are admitted into device slots while earlier ones are still
  * being evaluated, and share the device rounds with them.  A slot (used-vertex bitmap, window,
  * state: the device memory one request holds) is the admission unit; slots <= 0 sizes the
- * server from a quarter of the free device memory.  Two lanes, each with `slots` slots, its own
- * CUDA stream and host thread, run side by side: requests start in the light lane; one still
- * searching after 12 rounds is restarted in the heavy lane, so long searches do not slow the
- * rounds of short requests (256 candidate chunks per search and round in both).  The graph's options.deadline_ms, when set, bounds each request from its
+ * server from a quarter of the free device memory.  The server's host thread runs rounds of 256
+ * candidate chunks per search and request on its own CUDA stream.  The graph's options.deadline_ms, when set, bounds each request from its
  * submission: a request past it is reported with status FLEXIS_E_TIMEOUT (see flexis_options).
  * window_min / window_max / search_budget of the graph's options, when set, replace the
  * server's own defaults (start window 32, at most 2048).                                      */

@@ -725,13 +725,6 @@ int64_t flexis_generate_candidates(const flexis_pattern *frequent, int32_t count
 #include <deque>
 #include <mutex>
 
-// Two lanes, each a device session with its own slots, stream and host thread: every request
-// starts in the light lane; one still in its greedy phase after LIGHT_STEPS rounds is stopped
-// there and restarted in the heavy lane, so that requests needing long searches stop setting the
-// pace of the rounds every light request waits for (both lanes' rounds run side by side on the
-// device).  Results do not depend on the lane.
-constexpr int LIGHT_STEPS = 12;
-
 struct flexis_server {
     using clock = std::chrono::steady_clock;
     struct Req {
@@ -744,21 +737,16 @@ struct flexis_server {
         flexis_support_result res;
         double lat_us;
     };
-    struct Lane {
-        ServeSession *sess = nullptr;
-        int32_t slots = 0;
-        std::deque<Req> *queue = nullptr;  // where the lane admits from
-        int evict_after = 0;               // > 0: move requests still searching after this many steps
-        std::thread th;
-    };
     flexis_graph *g = nullptr;
-    Lane lanes[2];
+    ServeSession *sess = nullptr;
+    int32_t slots = 0;
     int32_t deadline_ms = 0;  // per request, from submission; 0 = none
+    std::thread th;
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
     int err = FLEXIS_OK;
-    std::deque<Req> pending, heavy;
+    std::deque<Req> pending;
     size_t max_pending = 1u << 20;
     std::deque<Done> done;
 
@@ -766,14 +754,11 @@ struct flexis_server {
         std::lock_guard<std::mutex> lk(mu);
         err = rc;
         stop = true;
-        cv.notify_all();
     }
 
-    void loop(Lane &L) {
-        const int32_t slots = L.slots;
+    void loop() {
         std::vector<Req> slot_req((size_t)slots);
-        std::vector<char> live((size_t)slots, 0), evicting((size_t)slots, 0);
-        std::vector<int32_t> steps((size_t)slots, 0);
+        std::vector<char> live((size_t)slots, 0);
         std::vector<int32_t> phase((size_t)slots, 0), admit, cancel;
         std::vector<Plan> aplans;
         std::vector<flexis_support_result> res((size_t)slots);
@@ -783,58 +768,46 @@ struct flexis_server {
             aplans.clear();
             {
                 std::unique_lock<std::mutex> lk(mu);
-                if (!stop && busy == 0 && L.queue->empty())
-                    cv.wait(lk, [&] { return stop || !L.queue->empty(); });
+                if (!stop && busy == 0 && pending.empty())
+                    cv.wait(lk, [&] { return stop || !pending.empty(); });
                 if (stop) break;
                 // admission: a free slot is the unit of device memory (used bitmap + window)
-                for (int32_t i = 0; i < slots && !L.queue->empty(); i++) {
+                for (int32_t i = 0; i < slots && !pending.empty(); i++) {
                     if (live[(size_t)i]) continue;
-                    slot_req[(size_t)i] = L.queue->front();
-                    L.queue->pop_front();
+                    slot_req[(size_t)i] = pending.front();
+                    pending.pop_front();
                     live[(size_t)i] = 1;
-                    evicting[(size_t)i] = 0;
-                    steps[(size_t)i] = 0;
                     admit.push_back(i);
                     aplans.push_back(slot_req[(size_t)i].plan);
                     busy++;
                 }
             }
             int32_t ng = 0;
-            int rc = serve_step(L.sess, admit.data(), aplans.data(), (int32_t)admit.size(), phase.data(),
+            int rc = serve_step(sess, admit.data(), aplans.data(), (int32_t)admit.size(), phase.data(),
                                 res.data(), &ng);
             if (rc) { fail(rc); break; }
             auto now = clock::now();
-            // requests past their deadline, and light-lane requests that keep searching, stop
-            // before the next step (which finalises them)
+            // requests past their deadline stop before the next step, which reports them
             cancel.clear();
-            for (int32_t i = 0; i < slots; i++) {
-                if (!live[(size_t)i] || phase[(size_t)i] == 3 || evicting[(size_t)i]) continue;
-                steps[(size_t)i]++;
-                const bool late = deadline_ms > 0 &&
-                    std::chrono::duration<double, std::milli>(now - slot_req[(size_t)i].t0).count() > deadline_ms;
-                const bool move = !late && L.evict_after > 0 && phase[(size_t)i] == 1 && steps[(size_t)i] >= L.evict_after;
-                if (late || move) cancel.push_back(i);
-                if (move) evicting[(size_t)i] = 1;
+            if (deadline_ms > 0) {
+                for (int32_t i = 0; i < slots; i++) {
+                    if (!live[(size_t)i] || phase[(size_t)i] == 3) continue;
+                    if (std::chrono::duration<double, std::milli>(now - slot_req[(size_t)i].t0).count() > deadline_ms)
+                        cancel.push_back(i);
+                }
             }
-            if (!cancel.empty() && (rc = serve_cancel(L.sess, cancel.data(), (int32_t)cancel.size())) != 0) {
+            if (!cancel.empty() && (rc = serve_cancel(sess, cancel.data(), (int32_t)cancel.size())) != 0) {
                 fail(rc);
                 break;
             }
             std::lock_guard<std::mutex> lk(mu);
-            bool moved = false;
             for (int32_t i = 0; i < slots; i++) {
                 if (!live[(size_t)i] || phase[(size_t)i] != 3) continue;
-                if (evicting[(size_t)i]) {
-                    heavy.push_back(slot_req[(size_t)i]);  // keeps its submission time
-                    moved = true;
-                } else {
-                    const double us = std::chrono::duration<double, std::micro>(now - slot_req[(size_t)i].t0).count();
-                    done.push_back(Done{slot_req[(size_t)i].id, res[(size_t)i], us});
-                }
+                const double us = std::chrono::duration<double, std::micro>(now - slot_req[(size_t)i].t0).count();
+                done.push_back(Done{slot_req[(size_t)i].id, res[(size_t)i], us});
                 live[(size_t)i] = 0;
                 busy--;
             }
-            if (moved) cv.notify_all();
         }
     }
 };
@@ -854,23 +827,12 @@ int flexis_serve_start(flexis_graph *g, int32_t slots, flexis_server **out) {
     }
     std::unique_ptr<flexis_server> s(new flexis_server());
     s->g = g;
+    s->slots = slots;
     s->deadline_ms = g->opt.deadline_ms;
-    flexis_server::Lane &light = s->lanes[0], &heavy = s->lanes[1];
-    light.slots = slots;
-    light.queue = &s->pending;
-    light.evict_after = LIGHT_STEPS;
-    heavy.slots = slots;
-    heavy.queue = &s->heavy;
-    int rc = serve_create(g->dg, light.slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &light.sess);
+    int rc = serve_create(g->dg, slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &s->sess);
     if (rc) return rc;
-    rc = serve_create(g->dg, heavy.slots, g->opt.window_min, g->opt.window_max, g->opt.search_budget, &heavy.sess);
-    if (rc) {
-        serve_destroy(light.sess);
-        return rc;
-    }
     flexis_server *raw = s.get();
-    light.th = std::thread([raw] { raw->loop(raw->lanes[0]); });
-    heavy.th = std::thread([raw] { raw->loop(raw->lanes[1]); });
+    s->th = std::thread([raw] { raw->loop(); });
     *out = s.release();
     return FLEXIS_OK;
 }
@@ -920,10 +882,9 @@ int flexis_serve_stop(flexis_server *s) {
         s->stop = true;
     }
     s->cv.notify_all();
-    for (auto &L : s->lanes)
-        if (L.th.joinable()) L.th.join();
+    if (s->th.joinable()) s->th.join();
     int err = s->err;
-    for (auto &L : s->lanes) serve_destroy(L.sess);
+    serve_destroy(s->sess);
     delete s;
     return err;
 }
