@@ -171,3 +171,17 @@ def test_candidate_generation_matches_oracle_predicate(k):
             F.append((lab, e))
         for me in (0, k + 1):
             assert fx.generate_candidates(F, me) == oracle.candidates(F, me)
+
+
+def test_lambda_quantisation_rounds_half_away_from_zero():
+    # lambda -> num / 10^6 with num = llround(lambda * 10^6): the double product rounded to the
+    # nearest integer, halves away from zero (the binding no longer rounds on its own)
+    from decimal import ROUND_HALF_UP, Decimal
+    st = Stream(31)
+    vals = [0.0, 1.0, 0.5, 0.25, 2.5e-6, 0.0000125, 0.1234565, 0.9999995] + list(st.uniform(200))
+    for lam in vals:
+        want = int(Decimal(float(lam) * 1e6).quantize(Decimal(1), rounding=ROUND_HALF_UP))
+        assert fx.lambda_quantize(float(lam)) == want, lam
+    for bad in (-1e-9, 1.0000001, float("nan")):
+        with pytest.raises(fx.FlexisError):
+            fx.lambda_quantize(bad)
