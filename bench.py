@@ -297,7 +297,7 @@ def reference_arm(args):
     return 0
 
 
-def batched_level_leg(fx, local, n_plain=200):
+def batched_level_leg(fx, local, n_plain=100):
     """1 M-vertex batched level: 2,000 candidates (trees, cycles, cliques of 3-7 vertices) of a
     Chung-Lu graph (1 M vertices, 10 M edges, 37 labels Zipf(1.0)) in one batched pass, against
     plain one-pattern calls (each launched and synchronised on its own) on the first n_plain."""
