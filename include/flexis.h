@@ -140,7 +140,11 @@ typedef struct {
                                 (power-of-two bucket) times a slice of itself under a few per-round
                                 search budgets and keeps the fastest for the graph; -1 = off (the
                                 built-in table).  Results never depend on it */
-    int32_t reserved[5];
+    int32_t host_build;      /* 0 = default: an undirected graph's layout is built on the device
+                                from the uploaded edge list (a radix sort of the arcs); 1 = built
+                                on the host and uploaded.  Both give the same arrays bit for bit;
+                                a directed graph is always built on the host */
+    int32_t reserved[4];
 } flexis_options;
 
 /* A query pattern: n vertices with labels[n] (label ids of the data graph), m undirected
@@ -201,6 +205,9 @@ typedef struct {
     int32_t edge_label_base;  /* label id of edge label 0 in the extended graph; -1 without
                                  edge labels */
     int32_t directed;         /* 1 for a directed graph (options.directed) */
+    int32_t built_on_device;  /* 1: the layout was built on the device (options.host_build) */
+    int64_t upload_bytes;     /* host-to-device bytes of the load: the edge list and vertex ranks
+                                 (device build) or the layout arrays (host build) */
 } flexis_graph_info;
 
 /* Counters of the last support / batch / mining call on a graph (diagnostics, timing). */
@@ -256,7 +263,9 @@ void flexis_default_options(flexis_options *opt);
  * loader, Sec. 4.1).  labels[n_vertices] >= 0; src/dst[n_edges] vertex ids in [0, n_vertices).
  * Self-loops and repeated edges are dropped (counted in flexis_graph_info).  The graph is kept
  * on the device as a CSR with adjacency sorted by (label rank, id), a per-vertex label-run table
- * and a label-partitioned vertex index in greedy-root order.
+ * and a label-partitioned vertex index in greedy-root order.  An undirected graph's layout is
+ * built on the device from the uploaded edge list (options.host_build selects the host builder;
+ * both give the same arrays); the caller's arrays are only read during the call.
  * Layout limits (FLEXIS_E_UNSUPPORTED beyond them): fewer than 255 distinct labels present,
  * n_vertices < 2^31, directed arcs < 2^32, vertex degree < 2^24.  opt may be NULL.             */
 int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges,
@@ -278,6 +287,21 @@ int flexis_load_graph_edge_labels(int64_t n_vertices, const int32_t *labels, int
                                   const flexis_options *opt, flexis_graph **out);
 void flexis_free_graph(flexis_graph *g);
 int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out);
+
+/* Copy one array of the resident layout to host memory (diagnostics and tests).  part:
+ * FLEXIS_LAYOUT_VREC (8 x uint32 per record: adjacency offset, run offset, degree,
+ * runs << 8 | rank label, the 64-bit set of neighbour rank labels < 64, 8 zero bytes; one record
+ * per vertex, three per vertex for a directed graph: out, in, mutual), FLEXIS_LAYOUT_RUNS
+ * (uint32: rank << 24 | slice offset per label run, then 0xFF << 24 | degree, per vertex),
+ * FLEXIS_LAYOUT_ADJ (int32 neighbour ids sorted by (rank label, id) per vertex) or
+ * FLEXIS_LAYOUT_LAB_VTX (int32 vertex ids grouped by rank label, in greedy-root order).
+ * *bytes receives the array's size; out == NULL only queries it; capacity (bytes) below that
+ * size is FLEXIS_E_INVALID.  Synchronous.                                                      */
+#define FLEXIS_LAYOUT_VREC 0
+#define FLEXIS_LAYOUT_RUNS 1
+#define FLEXIS_LAYOUT_ADJ 2
+#define FLEXIS_LAYOUT_LAB_VTX 3
+int flexis_graph_layout(const flexis_graph *g, int32_t part, void *out, int64_t capacity, int64_t *bytes);
 
 /* Support of one pattern (Sec. 2.4, Eq. tau): one plain evaluation, launched and synchronised
  * on its own.  lambda in [0,1]; mode FLEXIS_MODE_EARLY or FLEXIS_MODE_FULL.                    */

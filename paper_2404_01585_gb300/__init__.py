@@ -40,6 +40,10 @@ FLEXIS_FLAG_MNI_SATURATED = 16
 FLEXIS_FLAG_MAPS_SATURATED = 32
 FLEXIS_FLAG_MIS_SKIPPED = 64
 FLEXIS_FLAG_EXACT_MIS_SATURATED = 128
+FLEXIS_LAYOUT_VREC = 0
+FLEXIS_LAYOUT_RUNS = 1
+FLEXIS_LAYOUT_ADJ = 2
+FLEXIS_LAYOUT_LAB_VTX = 3
 LAMBDA_DEN = 1_000_000
 DEFAULT_SEED = 0x5EED
 
@@ -58,7 +62,8 @@ class flexis_options(C.Structure):
                 ("graphs", C.c_int32), ("deadline_ms", C.c_int32), ("root_order", C.c_int32),
                 ("directed", C.c_int32), ("maps_cap", C.c_int64),
                 ("frontier_rows", C.c_int64), ("exact_mis_nodes", C.c_int64),
-                ("exact_mis_maps", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("exact_mis_maps", C.c_int32), ("autotune", C.c_int32), ("host_build", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class flexis_pattern(C.Structure):
@@ -95,7 +100,8 @@ class flexis_graph_info(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("n_arcs", C.c_int64), ("n_self_loops", C.c_int64),
                 ("n_duplicates", C.c_int64), ("n_labels", C.c_int32), ("max_degree", C.c_int32),
                 ("device_bytes", C.c_int64), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32),
-                ("n_input_vertices", C.c_int64), ("edge_label_base", C.c_int32), ("directed", C.c_int32)]
+                ("n_input_vertices", C.c_int64), ("edge_label_base", C.c_int32), ("directed", C.c_int32),
+                ("built_on_device", C.c_int32), ("upload_bytes", C.c_int64)]
 
 
 class flexis_stats(C.Structure):
@@ -127,6 +133,7 @@ SYMBOLS = {
                                                  C.POINTER(flexis_options), C.POINTER(_P)]),
     "flexis_free_graph": (None, [_P]),
     "flexis_graph_info_get": (C.c_int, [_P, C.POINTER(flexis_graph_info)]),
+    "flexis_graph_layout": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _I64P]),
     "flexis_support": (C.c_int, [_P, C.POINTER(flexis_pattern), C.c_int64, C.c_double, C.c_int32,
                                   C.POINTER(flexis_support_result)]),
     "flexis_support_q": (C.c_int, [_P, C.POINTER(flexis_pattern), C.c_int64, C.c_int64, C.c_int64,
@@ -232,7 +239,7 @@ class Graph:
     Keyword options are the fields of flexis_options: seed, device, window_min, window_max,
     search_blocks, record_selected, search_budget, split_pieces, sub_searches, timing, graphs,
     deadline_ms, root_order, directed, maps_cap, frontier_rows, exact_mis_nodes,
-    exact_mis_maps, autotune (meanings in include/flexis.h).  They apply to every
+    exact_mis_maps, autotune, host_build (meanings in include/flexis.h).  They apply to every
     call on the graph and to servers started on it."""
 
     def __init__(self, labels, src, dst, edge_labels=None, **options):
@@ -279,6 +286,17 @@ class Graph:
         i = flexis_graph_info()
         _check(lib().flexis_graph_info_get(self._h, C.byref(i)), "flexis_graph_info_get")
         return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def layout(self, part: int) -> np.ndarray:
+        """One resident layout array (flexis_graph_layout): FLEXIS_LAYOUT_VREC as uint32 rows of
+        8 words, the others as flat uint32 / int32 arrays."""
+        n = C.c_int64()
+        _check(lib().flexis_graph_layout(self._h, part, None, 0, C.byref(n)), "flexis_graph_layout")
+        dt = np.uint32 if part in (FLEXIS_LAYOUT_VREC, FLEXIS_LAYOUT_RUNS) else np.int32
+        out = np.zeros(n.value // 4, dtype=dt)
+        _check(lib().flexis_graph_layout(self._h, part, out.ctypes.data_as(_P), n.value, C.byref(n)),
+               "flexis_graph_layout")
+        return out.reshape(-1, 8) if part == FLEXIS_LAYOUT_VREC else out
 
     def support(self, labels, edges, sigma, lam=None, *, lam_num=None, lam_den=LAMBDA_DEN,
                 mode=FLEXIS_MODE_EARLY, edge_labels=None) -> dict:

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflexis.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["kernels.cu", "enumerate.cu", "graph.cpp", "pattern.cpp", "api.cpp"]
+SOURCES = ["kernels.cu", "enumerate.cu", "graph_build.cu", "graph.cpp", "pattern.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -328,11 +328,25 @@ int flexis_load_graph(int64_t n_vertices, const int32_t *labels, int64_t n_edges
     std::unique_ptr<flexis_graph> g(new (std::nothrow) flexis_graph());
     if (!g) return FLEXIS_E_NOMEM;
     if (opt) g->opt = *opt; else flexis_default_options(&g->opt);
-    int rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1, g->hg,
+    int rc;
+    // the device build sorts 2 x n_edges arcs with 32-bit positions; a larger edge list (and a
+    // directed graph) is built on the host
+    if (!g->opt.directed && !g->opt.host_build && 2 * (uint64_t)std::max<int64_t>(n_edges, 0) < UINT32_MAX) {
+        rc = dev_graph_build(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1,
+                             g->opt.device, g->hg, &g->dg);
+        if (rc) return rc;
+    } else {
+        rc = build_host_graph(n_vertices, labels, n_edges, src, dst, g->opt.seed, g->opt.root_order == 1, g->hg,
                               g->opt.directed ? 1 : 0);
-    if (rc) return rc;
-    rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
-    if (rc) return rc;
+        if (rc) return rc;
+        rc = dev_graph_create(g->hg, g->opt.device, &g->dg);
+        if (rc) return rc;
+        // the layout lives on the device; the host keeps the label tables and counts
+        std::vector<VRec>().swap(g->hg.vrec);
+        std::vector<uint32_t>().swap(g->hg.runs);
+        std::vector<int32_t>().swap(g->hg.adj);
+        std::vector<int32_t>().swap(g->hg.lab_vtx);
+    }
     g->n_input_vertices = n_vertices;
     g->input_self_loops = g->hg.self_loops;
     g->input_duplicates = g->hg.duplicates;
@@ -395,6 +409,11 @@ int flexis_load_graph_edge_labels(int64_t n_vertices, const int32_t *labels, int
     return FLEXIS_OK;
 }
 
+int flexis_graph_layout(const flexis_graph *g, int32_t part, void *out, int64_t capacity, int64_t *bytes) {
+    if (!g || !bytes) return FLEXIS_E_INVALID;
+    return dev_graph_layout(g->dg, part, out, capacity, bytes);
+}
+
 void flexis_free_graph(flexis_graph *g) {
     if (!g) return;
     dev_graph_destroy(g->dg);
@@ -414,6 +433,7 @@ int flexis_graph_info_get(const flexis_graph *g, flexis_graph_info *out) {
     out->n_labels = g->hg.nl;
     out->max_degree = g->hg.max_degree;
     out->device_bytes = dev_graph_bytes(g->dg);
+    dev_graph_load_info(g->dg, &out->upload_bytes, &out->built_on_device);
     int sm = 0, l2 = 0;
     dev_graph_props(g->dg, &sm, &l2);
     out->sm_count = sm;

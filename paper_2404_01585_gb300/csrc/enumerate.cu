@@ -31,7 +31,6 @@ constexpr int ENUM_THREADS = 256;
 constexpr int ENUM_WARPS = ENUM_THREADS / 32;
 constexpr int64_t ENUM_DEFAULT_ROWS = 1ll << 22;
 constexpr unsigned long long DEFAULT_MAPS_CAP = 1ull << 32;
-constexpr int SCAN_TILE = 2048;  // elements per block of the scan (1024 threads x 2)
 
 // Algorithmic counters of the enumerator (device): rows extended, driver-slice entries scanned,
 // survivors, and bytes read (slices, records, probes).
@@ -287,6 +286,15 @@ __global__ void k_scan_add(unsigned long long *off, long long n, const unsigned 
     const long long a = (long long)blockIdx.x * SCAN_TILE + threadIdx.x;
     const unsigned long long add = tsum[blockIdx.x];
     for (long long x = a; x < min(n, (long long)(blockIdx.x + 1) * SCAN_TILE); x += blockDim.x) off[x] += add;
+}
+
+int dev_scan_u64(unsigned long long *cnt_off, long long n, unsigned long long *tsum, cudaStream_t s) {
+    const int tiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    if (tiles > 0) k_scan_tiles<<<tiles, 1024, 0, s>>>(cnt_off, cnt_off, n, tsum);
+    k_scan_tops<<<1, 1024, 0, s>>>(tsum, tiles, cnt_off, n);
+    if (tiles > 0) k_scan_add<<<tiles, 1024, 0, s>>>(cnt_off, n, tsum);
+    CK(cudaGetLastError());
+    return FLEXIS_OK;
 }
 
 // Largest e in (pos, end] with off[e] - off[pos] <= cap (at least pos + 1: one row's survivors
@@ -705,13 +713,8 @@ struct EnumRun {
     }
 
     int scan(unsigned long long *cnt_off, long long n) {
-        const int tiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
-        if (tiles > 0) k_scan_tiles<<<tiles, 1024, 0, s>>>(cnt_off, cnt_off, n, w->tsum);
-        k_scan_tops<<<1, 1024, 0, s>>>(w->tsum, tiles, cnt_off, n);
-        if (tiles > 0) k_scan_add<<<tiles, 1024, 0, s>>>(cnt_off, n, w->tsum);
         launches += 3;
-        CK(cudaGetLastError());
-        return FLEXIS_OK;
+        return dev_scan_u64(cnt_off, n, w->tsum, s);
     }
 
     // read one device word (synchronises the stream)

@@ -95,6 +95,10 @@ struct HostGraph {
 uint64_t root_hash(uint64_t seed, int64_t r);
 
 // host graph construction (graph.cpp)
+// Label tables of a graph (nl_ids, nl, rank_of, label_of_rank, lab_ptr) and the rank of every
+// vertex (rk[max(nv, 1)]); FLEXIS_E_INVALID for a negative label, FLEXIS_E_UNSUPPORTED for 255
+// or more labels present.
+int label_ranks(int64_t nv, const int32_t *labels, HostGraph &g, std::vector<uint8_t> &rk);
 int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
                      const int32_t *dst, uint64_t seed, int id_order, HostGraph &out,
                      int directed = 0);

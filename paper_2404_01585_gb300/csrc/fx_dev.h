@@ -30,6 +30,16 @@ struct EvalConfig {
 };
 
 int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out);
+// Undirected layout built on the device from the caller's edge list (graph_build.cu): the same
+// arrays as build_host_graph + dev_graph_create, bit for bit; hg receives the label tables,
+// lab_ptr, label pairs and counts, and no layout arrays.
+int dev_graph_build(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src, const int32_t *dst,
+                    uint64_t seed, int id_order, int device, HostGraph &hg, DeviceGraph **out);
+// Host-to-device bytes of the load, and whether the layout was built on the device.
+void dev_graph_load_info(const DeviceGraph *g, int64_t *upload_bytes, int32_t *on_device);
+// Copy one resident layout array to host memory (0 vrec, 1 runs, 2 adj, 3 lab_vtx); *bytes gets
+// its size; out may be NULL to query it.
+int dev_graph_layout(const DeviceGraph *g, int32_t part, void *out, int64_t cap, int64_t *bytes);
 void dev_graph_destroy(DeviceGraph *g);
 int dev_graph_device(const DeviceGraph *g);
 int64_t dev_graph_bytes(const DeviceGraph *g);

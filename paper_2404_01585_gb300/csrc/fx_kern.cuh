@@ -372,6 +372,9 @@ struct DeviceGraph {
     DevGraphView view{};
     void *d_vrec = nullptr, *d_runs = nullptr, *d_adj = nullptr, *d_labvtx = nullptr;
     int64_t bytes = 0;
+    int64_t upload_bytes = 0;  // host-to-device bytes of the load (layout arrays, or the edge list)
+    int32_t built_on_device = 0;
+    int64_t vrec_count = 0, runs_words = 0, adj_words = 0, labvtx_words = 0;  // allocated sizes
     int sm_count = 0, l2 = 0;
     Workspace ws;
     int32_t last_P = 0, last_sel = 0;
@@ -392,5 +395,14 @@ int dev_enumerate(DeviceGraph *g, const Plan *d_plans, int32_t P, flexis_support
                   cudaStream_t stream, const EvalConfig &cfg, flexis_stats *stats,
                   std::chrono::steady_clock::time_point t_start);
 void enum_ws_destroy(DeviceGraph *g);
+
+// Exclusive prefix sum of cnt_off[0, n) in place, cnt_off[n] set to the total (enumerate.cu).
+// tsum: scratch of scan_tsum_len(n) words.  Three launches on s.
+constexpr int SCAN_TILE = 2048;  // elements per block of the scan (1024 threads x 2)
+inline long long scan_tsum_len(long long n) { return n / SCAN_TILE + 2; }
+int dev_scan_u64(unsigned long long *cnt_off, long long n, unsigned long long *tsum, cudaStream_t s);
+
+// The object, stream, events and kernel attributes of a device graph, with no arrays (kernels.cu).
+int dev_graph_init(int device, DeviceGraph **out);
 
 }  // namespace fx

@@ -181,21 +181,12 @@ static int build_directed(int64_t nv, int64_t ne, const int32_t *src, const int3
     return FLEXIS_OK;
 }
 
-int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
-                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &g, int directed) {
-    if (nv < 0 || ne < 0 || (nv > 0 && !labels) || (ne > 0 && (!src || !dst)))
-        return FLEXIS_E_INVALID;
-    if (nv >= (int64_t)INT32_MAX) return FLEXIS_E_UNSUPPORTED;
-    g = HostGraph();
-    g.nv = nv;
-    g.seed = seed;
+int label_ranks(int64_t nv, const int32_t *labels, HostGraph &g, std::vector<uint8_t> &rk) {
     int32_t nl_ids = 0;
     for (int64_t v = 0; v < nv; v++) {
         if (labels[v] < 0) return FLEXIS_E_INVALID;
         nl_ids = std::max(nl_ids, labels[v] + 1);
     }
-    for (int64_t e = 0; e < ne; e++)
-        if (src[e] < 0 || dst[e] < 0 || src[e] >= nv || dst[e] >= nv) return FLEXIS_E_INVALID;
     g.nl_ids = nl_ids;
     // label ranks: ascending frequency, ties by id
     std::vector<int64_t> cnt((size_t)nl_ids, 0);
@@ -210,9 +201,31 @@ int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_
     g.nl = (int32_t)present.size();
     g.rank_of.assign((size_t)nl_ids, -1);
     g.label_of_rank = present;
-    for (size_t r = 0; r < present.size(); r++) g.rank_of[(size_t)present[r]] = (int32_t)r;
-    std::vector<uint8_t> rk((size_t)std::max<int64_t>(nv, 1));
+    g.lab_ptr.assign((size_t)g.nl + 1, 0);
+    for (size_t r = 0; r < present.size(); r++) {
+        g.rank_of[(size_t)present[r]] = (int32_t)r;
+        g.lab_ptr[r + 1] = g.lab_ptr[r] + (int32_t)cnt[(size_t)present[r]];
+    }
+    rk.assign((size_t)std::max<int64_t>(nv, 1), 0);
     for (int64_t v = 0; v < nv; v++) rk[(size_t)v] = (uint8_t)g.rank_of[(size_t)labels[v]];
+    return FLEXIS_OK;
+}
+
+int build_host_graph(int64_t nv, const int32_t *labels, int64_t ne, const int32_t *src,
+                     const int32_t *dst, uint64_t seed, int id_order, HostGraph &g, int directed) {
+    if (nv < 0 || ne < 0 || (nv > 0 && !labels) || (ne > 0 && (!src || !dst)))
+        return FLEXIS_E_INVALID;
+    if (nv >= (int64_t)INT32_MAX) return FLEXIS_E_UNSUPPORTED;
+    g = HostGraph();
+    g.nv = nv;
+    g.seed = seed;
+    for (int64_t v = 0; v < nv; v++)
+        if (labels[v] < 0) return FLEXIS_E_INVALID;
+    for (int64_t e = 0; e < ne; e++)
+        if (src[e] < 0 || dst[e] < 0 || src[e] >= nv || dst[e] >= nv) return FLEXIS_E_INVALID;
+    std::vector<uint8_t> rk;
+    const int lrc = label_ranks(nv, labels, g, rk);
+    if (lrc) return lrc;
     g.directed = directed ? 1 : 0;
     if (directed) {
         std::vector<int32_t> rk32(rk.begin(), rk.end());

@@ -929,28 +929,14 @@ int dev_free_bytes(const DeviceGraph *g, int64_t *bytes) {
     return FLEXIS_OK;
 }
 
-int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
+int dev_graph_init(int device, DeviceGraph **out) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) return FLEXIS_E_CUDA;
     DeviceGraph *g = new DeviceGraph();
     g->device = device;
-    int rc = FLEXIS_OK;
     auto fail = [&](int code) { dev_graph_destroy(g); return code; };
     if (cudaSetDevice(device) != cudaSuccess) return fail(FLEXIS_E_CUDA);
     if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FLEXIS_E_CUDA);
-    if ((rc = upload(&g->d_vrec, hg.vrec, g->stream, g->bytes))) return fail(rc);
-    if ((rc = upload(&g->d_runs, hg.runs, g->stream, g->bytes))) return fail(rc);
-    if ((rc = upload(&g->d_adj, hg.adj, g->stream, g->bytes))) return fail(rc);
-    if ((rc = upload(&g->d_labvtx, hg.lab_vtx, g->stream, g->bytes))) return fail(rc);
-    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(FLEXIS_E_CUDA);
-    g->view.vrec = (const VRec *)g->d_vrec;
-    g->view.runs = (const uint32_t *)g->d_runs;
-    g->view.adj = (const int32_t *)g->d_adj;
-    g->view.lab_vtx = (const int32_t *)g->d_labvtx;
-    g->view.nv = hg.nv;
-    g->view.words = (int32_t)std::max<int64_t>(1, (hg.nv + 31) / 32);
-    g->view.dstride = hg.directed ? hg.nv : 0;
-    g->max_degree = hg.max_degree;
     if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
         cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)
@@ -967,6 +953,33 @@ int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
             per_sm = 1;
         g->commit_small_blocks = g->sm_count * std::max(1, per_sm);
     }
+    *out = g;
+    return FLEXIS_OK;
+}
+
+int dev_graph_create(const HostGraph &hg, int device, DeviceGraph **out) {
+    DeviceGraph *g = nullptr;
+    int rc = dev_graph_init(device, &g);
+    if (rc) return rc;
+    auto fail = [&](int code) { dev_graph_destroy(g); return code; };
+    if ((rc = upload(&g->d_vrec, hg.vrec, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_runs, hg.runs, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_adj, hg.adj, g->stream, g->bytes))) return fail(rc);
+    if ((rc = upload(&g->d_labvtx, hg.lab_vtx, g->stream, g->bytes))) return fail(rc);
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(FLEXIS_E_CUDA);
+    g->upload_bytes = g->bytes;
+    g->vrec_count = (int64_t)std::max<size_t>(hg.vrec.size(), 1);
+    g->runs_words = (int64_t)std::max<size_t>(hg.runs.size(), 1);
+    g->adj_words = (int64_t)std::max<size_t>(hg.adj.size(), 1);
+    g->labvtx_words = (int64_t)std::max<size_t>(hg.lab_vtx.size(), 1);
+    g->view.vrec = (const VRec *)g->d_vrec;
+    g->view.runs = (const uint32_t *)g->d_runs;
+    g->view.adj = (const int32_t *)g->d_adj;
+    g->view.lab_vtx = (const int32_t *)g->d_labvtx;
+    g->view.nv = hg.nv;
+    g->view.words = (int32_t)std::max<int64_t>(1, (hg.nv + 31) / 32);
+    g->view.dstride = hg.directed ? hg.nv : 0;
+    g->max_degree = hg.max_degree;
     *out = g;
     return FLEXIS_OK;
 }
@@ -1037,6 +1050,30 @@ void dev_graph_destroy(DeviceGraph *g) {
 
 int dev_graph_device(const DeviceGraph *g) { return g->device; }
 int64_t dev_graph_bytes(const DeviceGraph *g) { return g->bytes; }
+
+void dev_graph_load_info(const DeviceGraph *g, int64_t *upload_bytes, int32_t *on_device) {
+    *upload_bytes = g->upload_bytes;
+    *on_device = g->built_on_device;
+}
+
+int dev_graph_layout(const DeviceGraph *g, int32_t part, void *out, int64_t cap, int64_t *bytes) {
+    const void *src = nullptr;
+    int64_t size = 0;
+    switch (part) {
+        case 0: src = g->d_vrec; size = g->vrec_count * (int64_t)sizeof(VRec); break;
+        case 1: src = g->d_runs; size = g->runs_words * 4; break;
+        case 2: src = g->d_adj; size = g->adj_words * 4; break;
+        case 3: src = g->d_labvtx; size = g->labvtx_words * 4; break;
+        default: return FLEXIS_E_INVALID;
+    }
+    *bytes = size;
+    if (!out) return FLEXIS_OK;
+    if (cap < size) return FLEXIS_E_INVALID;
+    CK(cudaSetDevice(g->device));
+    CK(cudaMemcpyAsync(out, src, (size_t)size, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return FLEXIS_OK;
+}
 cudaStream_t dev_graph_stream(const DeviceGraph *g) { return g->stream; }
 int dev_graph_props(const DeviceGraph *g, int *sm, int *l2) {
     *sm = g->sm_count;
