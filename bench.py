@@ -11,7 +11,8 @@ runs) counts as one support evaluation.
           (CUDA events on the library's stream around the K timed steps; L2 flushed between
           steps by a 256 MiB write).
   e2e   : the same metric through the public API from host buffers: every step loads the graph
-          from host arrays (flexis_load_graph), mines, reads the frequent sets back.
+          from host arrays (flexis_load_graph: edge list uploaded, layout built on the device),
+          mines, reads the frequent sets back.
   roofline : the dominant kernel (the greedy search kernel): algorithmic bytes B counted on the
           device (4 per label-slice entry scanned, 8 per bound vertex of every partial map -- one
           write, one read -- and 4 per vertex of every map found) over its summed CUDA-event
@@ -479,7 +480,7 @@ def main():
             st = g2.stats()
             h2d += st["h2d_bytes"]
             d2h += st["d2h_bytes"] + 96 * int(arr["n"].size)
-        h2d += info["device_bytes"]
+        h2d += info["upload_bytes"]  # the edge list and vertex ranks (the layout is built on the device)
         g2.close()
         torch.cuda.synchronize()
         e2e_t += time.perf_counter() - t0
