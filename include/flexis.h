@@ -350,7 +350,7 @@ int flexis_support_plans_device(flexis_graph *g, const flexis_plan *d_plans, int
  * up to about 66 million vertices; larger graphs return FLEXIS_E_UNSUPPORTED with the exact limit
  * printed on stderr.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
- * device); make that first call before any stream capture.  Every call on a device shares the
+ * device).  Every call on a device shares the
  * array and it keeps the last call's contents (the call clears what must start at zero): calls
  * whose work overlaps on the GPU -- on different streams or from different threads -- race, so
  * serialise them.                                                                               */

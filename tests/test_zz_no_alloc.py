@@ -1,5 +1,5 @@
-"""The allocation-free entry point (flexis_support_noalloc) gives the same supports as
-flexis_support.
+"""The allocation-free entry point (flexis_support_noalloc) gives the oracle's supports and the
+same supports as flexis_support.
 
 It serves callers that cannot call cudaMalloc while evaluating: its device scratch is one static
 device array shared by every call on a GPU, so this file runs last (pytest collects it last) and
@@ -7,8 +7,10 @@ calls the entry point twice in a row to check that the second call starts from a
 although the array keeps the first call's contents."""
 from __future__ import annotations
 
+import numpy as np
 import pytest
 
+import oracle
 import paper_2404_01585_gb300 as fx
 from workloads import make_graph, random_patterns
 
@@ -79,3 +81,43 @@ def test_noalloc_honours_the_deadline(graph_and_patterns):
         else:
             assert key(got) == key(want[i])
     g.close()
+
+
+def test_noalloc_matches_the_oracle(graph_and_patterns):
+    # every pattern the oracle finishes within its search budget, in both modes
+    lab, src, dst, pats = graph_and_patterns
+    og = oracle.Graph(lab, src, dst)
+    g = fx.Graph(lab, src, dst)
+    compared = 0
+    for mode, omode in ((fx.FLEXIS_MODE_EARLY, "early"), (fx.FLEXIS_MODE_FULL, "full")):
+        plans = g.compile(pats, 60, 0.5, mode)
+        for i, (pl, pe) in enumerate(pats):
+            w = og.support(list(pl), [tuple(e) for e in np.asarray(pe).tolist()], sigma=60, lam=0.5, mode=omode,
+                           budget=20_000_000)
+            if w is None:
+                continue
+            got = g.support_noalloc(plans[i])
+            assert key(got) == (0, w["tau"], w["mis"], w["mni"], w["frequent"]), (pl, pe, got, w)
+            compared += 1
+    assert compared >= 16
+    g.close()
+
+
+def test_noalloc_vertex_limit():
+    # the used-vertex bitmap must fit the static array beside the other scratch: about 66 million
+    # vertices; a graph within it evaluates, one beyond it is refused (and nothing runs)
+    pats = [([0, 0], [(0, 1)])]
+    for nv, ok in ((60_000_000, True), (70_000_000, False)):
+        lab = np.zeros(nv, np.int32)
+        src = np.arange(0, 2000, 2, dtype=np.int32)
+        g = fx.Graph(lab, src, src + 1)
+        plan = g.compile(pats, 10, 0.5, fx.FLEXIS_MODE_EARLY)[0]
+        if ok:
+            got = g.support_noalloc(plan)
+            assert key(got) == key(g.support(*pats[0], 10, 0.5, mode=fx.FLEXIS_MODE_EARLY))
+            assert got["frequent"] and got["mis"] == got["tau"] > 0  # 1000 disjoint edges, capped at tau
+        else:
+            with pytest.raises(fx.FlexisError) as e:
+                g.support_noalloc(plan)
+            assert e.value.code == fx.FLEXIS_E_UNSUPPORTED
+        g.close()
