@@ -201,9 +201,22 @@ struct SearchWork {
     uint32_t scanned = 0, bound = 0;  // per search: at most budget x 32 entries
 };
 
+// Drain: once most warps of a search launch have run out of work items, the searches still
+// running suspend at their next check (every DRAIN_EVERY chunks, after DRAIN_MIN_STEPS) instead
+// of running to the round's budget, so the launch ends and the next round starts; a suspended
+// search resumes (and may be split) there.  Suspension points never change a result.
+constexpr uint32_t DRAIN_EVERY = 16;
+constexpr uint32_t DRAIN_MIN_STEPS = 32;
+
+__device__ __forceinline__ bool drain_requested(const int32_t *drain) {
+    int d = 0;
+    if ((threadIdx.x & 31) == 0) d = *reinterpret_cast<const volatile int32_t *>(drain);
+    return __shfl_sync(FULLMASK, d, 0) != 0;
+}
+
 __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_t *used, int32_t root,
                        unsigned long long &bytes, uint32_t &probes, uint32_t &steps, uint32_t budget,
-                       bool resume, SearchWork &work) {
+                       bool resume, SearchWork &work, const int32_t *drain = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n = W.n;
     int i = 1;
@@ -247,7 +260,8 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
         }
         if (mask == 0) {
             if (pos >= hi) { ok = false; continue; }
-            if (budget && steps >= budget) {
+            if (budget && (steps >= budget || (drain && steps >= DRAIN_MIN_STEPS && steps % DRAIN_EVERY == 0 &&
+                                               drain_requested(drain)))) {
                 if (lane == 0) {
                     W.level = i;
                     W.hi[i] = hi; W.pos[i] = pos; W.base[i] = base; W.mask[i] = 0; W.conf[i] = conf;
@@ -261,7 +275,7 @@ __device__ inline int dfs_run(const DevGraphView &G, WarpState &W, const uint32_
             if (k < hi) good = check_candidate(G, W, i, __ldg(G.adj + k), used, probes, rej);
             mask = __ballot_sync(FULLMASK, good);
             conf |= __reduce_or_sync(FULLMASK, rej);
-            work.scanned += min(32u, hi - pos);  // 4 bytes each, added to the touched bytes at the end
+            work.scanned += min(32u, hi - pos);  // slice entries scanned: 4 bytes each in the algorithmic bytes
             steps++;
             base = pos;
             pos += 32;

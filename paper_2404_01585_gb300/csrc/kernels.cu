@@ -4,7 +4,7 @@
 //   mIS  : the greedy maximal independent set of the pattern's maps (Sec. 2.4.3) taken in the
 //          fixed order (H(seed, root), root, lexicographic tuple in matching order): roots are
 //          visited in hash order (or by vertex id, the root-order variant; the order lives only
-//          in the host-built root index), each root selects its lexicographically first map that
+//          in the root index built at load), each root selects its lexicographically first map that
 //          avoids vertices already used and then stops (Sec. 3.2.2, changes 1 and 2).  EARLY
 //          mode stops at c = max(tau, 1) selections (Sec. 3.1.1).
 //   MNI  : min over automorphism orbits of the number of distinct data vertices that some map
@@ -80,6 +80,8 @@ struct Ctl {
     int32_t next_item[2];
     int32_t active[2];
     int32_t acount[2];    // lengths of the two active-pattern lists
+    int32_t idle[2];      // warps of the search launch that found no work item left
+    int32_t drain[2];     // set once idle reaches the launch's drain threshold
     int32_t err;
     int32_t pad;
     unsigned long long bytes_greedy;
@@ -139,6 +141,7 @@ constexpr uint32_t SEARCH_BUDGET = 4096;  // candidate chunks a root search runs
 
 // ------------------------------------------------------------------ kernels
 constexpr int SEARCH_THREADS = 256;
+constexpr int DRAIN_DIV = 8;  // the searches drain once all but 1/DRAIN_DIV of the launch's warps are idle
 constexpr int DIRTY_CAP = 1024;  // listed used-bitmap words per pattern (4 KB)
 constexpr int COMMIT_THREADS = 256;
 
@@ -146,6 +149,8 @@ __device__ void reset_ctl(Ctl *c) {
     c->n_items[0] = c->n_items[1] = 0;
     c->next_item[0] = c->next_item[1] = 0;
     c->active[0] = c->active[1] = 0;
+    c->idle[0] = c->idle[1] = 0;
+    c->drain[0] = c->drain[1] = 0;
     c->err = 0;
     c->bytes_greedy = c->bytes_mni = 0;
     c->alg_scanned = c->alg_bound = c->alg_map_words = 0;
@@ -218,7 +223,10 @@ __device__ __forceinline__ void save_state(uint32_t *dst, const WarpState &W, in
 // root avoiding the used set.  Item (pattern, slot, saved sub-search): continue that sub-search.
 // A search that uses up its per-round budget is saved; if it heads its slot it is also split:
 // the unscanned candidates of its shallowest level with any left go to up to five new
-// sub-searches, in order, and a continuation takes over everything after them.
+// sub-searches, in order, and a continuation takes over everything after them.  Once all but an
+// eighth of the launch's warps have found the item list empty, the searches still running are
+// saved (and split) the same way at their next drain check instead of running to the budget,
+// so a launch is not held open by a few long searches while most of the GPU idles.
 __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
     __shared__ WarpState ws[SEARCH_THREADS / 32];
     const int lane = threadIdx.x & 31;
@@ -235,7 +243,14 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&B.ctl->next_item[q], 1);
         it = __shfl_sync(FULLMASK, it, 0);
-        if (it >= n_items) break;
+        if (it >= n_items) {
+            // out of items: count this warp; past the threshold the running searches drain
+            if (lane == 0) {
+                const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+                if (atomicAdd(&B.ctl->idle[q], 1) + 1 >= nw - nw / DRAIN_DIV) B.ctl->drain[q] = 1;
+            }
+            break;
+        }
         const int2 item = B.items[it];
         const int p = item.x;
         const int off = item.y & 0xFFFFFF;
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 6) k_search(Batch B, int q) {
             __syncwarp();
         }
         uint32_t steps = 0;
-        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work);
+        int r = dfs_run(B.G, W, used, root, bytes, probes, steps, B.budget, resume, work, &B.ctl->drain[q]);
         if (lane == 0) {
             W.acc_scanned += work.scanned;
             W.acc_bound += work.bound;
@@ -685,6 +700,8 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_commit(Batch B, int q) {
         B.ctl->n_items[q ^ 1] = 0;
         B.ctl->next_item[q ^ 1] = 0;
         B.ctl->active[q ^ 1] = 0;
+        B.ctl->idle[q ^ 1] = 0;
+        B.ctl->drain[q ^ 1] = 0;
     }
     if (!B.alist) {
         commit_one<KM>(B, q, blockIdx.x, smem);
