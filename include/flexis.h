@@ -106,7 +106,9 @@ typedef struct {
     int32_t search_blocks;/* blocks of the search kernel: 0 = autotuned (multiple of the SM count) */
     int32_t record_selected; /* >0: keep up to this many selected maps per pattern (tests) */
     int32_t search_budget;   /* candidate chunks a root search runs per round before it is
-                                suspended and resumed in the next round: 0 = default, -1 = never */
+                                suspended and resumed in the next round (earlier, after 32 chunks,
+                                once nearly all of the search launch is out of work): 0 = default,
+                                -1 = never */
     int32_t split_pieces;    /* pieces a suspended search heading its slot is split into per round:
                                 0 = default, -1 = never split */
     int32_t sub_searches;    /* saved sub-searches a pattern may hold at once (1..32): 0 = default */
